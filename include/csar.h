@@ -1,0 +1,172 @@
+/*
+ * csar.h — C ABI of libcsar: compressed-sensing SAR imaging with a chirp-scaling
+ * approximated observation, on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes the iterative thresholding algorithm of the paper's
+ * Algorithm 1 / Eq. (25),
+ *
+ *     X <- T_sigma( X + mu * M( S . (Y - G(X)) ) ),
+ *
+ * where M is the chirp-scaling focusing operator (Section III-D: the approximated
+ * observation may be built from the inverse of the Chirp-Scaling Algorithm), G is
+ * its inverse with conjugate phases in reverse order (Section III-C, Eq. (18)),
+ * S is the sub-Nyquist sampling mask (the sampling operators Theta_eta, Theta_tau
+ * of Eq. (24) generalised to a 2-D mask) and T_sigma is complex soft or half
+ * thresholding at sigma = |b|_(K+1), the (K+1)-th largest magnitude of
+ * b = X + mu * Delta X (Section IV-B).
+ *
+ * Conventions (all entry points):
+ *  - Arrays are row-major [n_az][n_rg] complex64 (interleaved float re, im):
+ *    rows = pulses (azimuth, slow time), columns = range bins (fast time).
+ *    Range bin n_rg/2 is the scene-centre range r0; pulse n_az/2 is azimuth time 0.
+ *  - The DFT is unnormalised forward, 1/N inverse, on a circular grid with no
+ *    padding: M is exactly unitary and G = M^-1 = M^H (Theorem 1).
+ *  - Sampling masks are bit-packed row-major: bit j of 32-bit word w is element
+ *    32*w + j; a set bit marks a sampled echo element.
+ *  - Pointers named *_dev are device pointers (cudaMalloc'd or equivalent) owned
+ *    by the caller; the library never frees them.  Pointers named *_host are host
+ *    pointers (pageable or pinned).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Entry points taking device pointers only enqueue work on `stream` and return
+ *    without synchronising, unless documented otherwise.
+ *  - Every entry point returns a csar_status.  Invalid arguments are rejected on
+ *    the host before any launch; the message is available from csar_last_error()
+ *    (thread-local).  Errors detected on the device (non-finite data, capacity)
+ *    are latched in the plan and reported by csar_plan_check() and by the next
+ *    synchronising call.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the
+ *    caller (they share the plan's workspace).
+ */
+#ifndef CSAR_H
+#define CSAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CSAR_OK = 0,
+  CSAR_E_INVALID = 1,      /* bad argument (null pointer, size, range)                 */
+  CSAR_E_UNSUPPORTED = 2,  /* valid but outside what the kernels cover                  */
+  CSAR_E_OOM = 3,          /* device allocation failed                                 */
+  CSAR_E_CUDA = 4,         /* a CUDA runtime call failed                                */
+  CSAR_E_TIMEOUT = 5,      /* a bounded device-side wait expired                        */
+  CSAR_E_NONFINITE = 6,    /* NaN or Inf met in the echo or the iterate                 */
+  CSAR_E_INTERNAL = 7      /* internal capacity / consistency check failed              */
+} csar_status;
+
+/* System parameters (the paper's Table 2 rows: slant range of scene centre R_c,
+ * effective velocity V, centre frequency f0 = c / wavelength, PRF, range FM rate
+ * K_r = bandwidth / pulse_len, pulse duration, range sampling rate F_r).
+ * Zero squint, zero Doppler centroid. */
+typedef struct {
+  int32_t n_az;        /* N_a: rows (pulses); power of two, 16 .. 8192              */
+  int32_t n_rg;        /* N_r: columns (range bins); power of two, 16 .. 8192       */
+  double wavelength;   /* lambda [m]                                                 */
+  double velocity;     /* effective radar velocity V [m/s]                           */
+  double r0;           /* slant range of the scene centre (bin n_rg/2) = R_ref [m]  */
+  double prf;          /* pulse repetition frequency [Hz]                            */
+  double bandwidth;    /* chirp bandwidth B [Hz] (up-chirp)                          */
+  double pulse_len;    /* pulse duration T_p [s]                                     */
+  double fs;           /* range sampling rate [Hz]                                   */
+  double antenna_len;  /* La [m]; not used by G or M (kept for completeness)         */
+  double c;            /* speed of light [m/s]; 0 selects 299792458                  */
+} csar_params;
+
+typedef struct csar_plan_s* csar_plan;
+
+enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };
+enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1 };
+
+/* Options of the iterative thresholding algorithm (Algorithm 1, Section IV-B). */
+typedef struct {
+  int64_t K;          /* sparsity: sigma = (K+1)-th largest |b|; K >= n keeps all      */
+  int32_t iters;      /* number of iterations I (csar_solve)                           */
+  int32_t mu_mode;    /* CSAR_MU_FIXED or CSAR_MU_NIHT (adaptive step)                 */
+  float mu;           /* fixed step (CSAR_MU_FIXED); must be > 0                       */
+  int32_t thresh;     /* CSAR_THRESH_SOFT (q = 1) or CSAR_THRESH_HALF (q = 1/2)        */
+} csar_opts;
+
+/* Per-iteration diagnostics, host arrays of length >= opts.iters (any may be NULL). */
+typedef struct {
+  double* resid_sq;   /* ||S . (Y - G(X^(i)))||^2                                       */
+  float* mu;          /* step mu_i                                                      */
+  float* sigma;       /* lambda_i mu_i = |b|_(K+1)                                      */
+  int64_t* nnz;       /* nonzeros of X^(i+1)                                             */
+} csar_stats;
+
+/* Create a plan: validates `params`, builds the FP64 phase-coefficient tables of
+ * the chirp-scaling functions H1 (chirp scaling), H2 (range compression, SRC and
+ * bulk RCMC) and H3 (azimuth matched filter and residual phase) and uploads them,
+ * and allocates the plan's device workspace.  `flags` must be 0.  The plan uses the
+ * current CUDA device.  On error *out is set to NULL.  CSAR_E_UNSUPPORTED if the
+ * geometry's phase arguments exceed what the on-the-fly phase evaluation covers
+ * (|range-linear term| >= 2^22 cycles). */
+csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out);
+
+/* Destroy a plan (synchronises the device, frees the workspace).  NULL is a no-op. */
+csar_status csar_plan_destroy(csar_plan plan);
+
+/* y_dev = G(x_dev): the approximated observation (Section III-C/D, Eq. (18) with
+ * chirp-scaling sub-operations): azimuth FFT, x conj(H3), range FFT, x conj(H2),
+ * range IFFT, x conj(H1), azimuth IFFT.  x_dev, y_dev: n_az*n_rg complex64 device
+ * arrays; x_dev == y_dev (in place) is allowed; otherwise they must not overlap. */
+csar_status csar_G(csar_plan plan, const void* x_dev, void* y_dev, void* stream);
+
+/* x_dev = M(y_dev) = G^H(y_dev): chirp-scaling focusing (Section III-A Eq. (10),
+ * Section III-D): azimuth FFT, x H1, range FFT, x H2, range IFFT, x H3, azimuth
+ * IFFT.  Same layout and aliasing rules as csar_G. */
+csar_status csar_M(csar_plan plan, const void* y_dev, void* x_dev, void* stream);
+
+/* One iteration of Algorithm 1 (Eq. (25)) on device data:
+ *   X_dev <- T_sigma(X + mu M(S . (Y - G(X)))).
+ * Y_dev: echo, n complex64 (values where the mask bit is clear are ignored).
+ * mask_dev: bit-packed sampling mask, n/32 uint32.  X_dev: in/out, n complex64
+ * (any number of nonzeros on input; at most K on output).  sigma_dev: optional
+ * device float receiving sigma (NULL to skip).  The step is opts->mu (FIXED) or the
+ * NIHT step (NIHT; for an all-zero X the support is the top K of |Delta X|). */
+csar_status csar_ita_step(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                          void* X_dev, const csar_opts* opts, float* sigma_dev,
+                          void* stream);
+
+/* Algorithm 1 from X^(0) = 0 for opts->iters iterations; the K-sparse iterate stays
+ * on the device as a (index, value) list between iterations and X_dev (n complex64,
+ * output only) receives X^(I).  Each iteration is one CUDA graph launch.  If
+ * `stats` is non-NULL the call synchronises `stream` and fills the host arrays. */
+csar_status csar_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                       void* X_dev, const csar_opts* opts, const csar_stats* stats,
+                       void* stream);
+
+/* csar_solve from HOST buffers: copies Y_host (n complex64) and mask_host (n/32
+ * uint32) into plan-owned device buffers, runs csar_solve, copies X^(I) back into
+ * X_host (n complex64), and synchronises `stream` before returning. */
+csar_status csar_solve_host(csar_plan plan, const void* Y_host, const uint32_t* mask_host,
+                            void* X_host, const csar_opts* opts, const csar_stats* stats,
+                            void* stream);
+
+/* csar_solve without graphs, with CUDA events recorded on `stream` around every
+ * pass: pass_ms[0..5] receive the summed device time of the passes C1 (sparse
+ * azimuth FFT), R1 (range pass of G), C2 (residue), R2 (range pass of M), C3
+ * (Delta X, histogram, candidates) and the selection + threshold kernels, over
+ * opts->iters iterations.  n_pass must be >= 6.  Synchronises `stream`. */
+csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                               void* X_dev, const csar_opts* opts, float* pass_ms,
+                               int32_t n_pass, void* stream);
+
+/* Synchronise the plan's device and report (and clear) any latched device-side
+ * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, ...). */
+csar_status csar_plan_check(csar_plan plan);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* csar_last_error(void);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+int32_t csar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSAR_H */

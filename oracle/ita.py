@@ -110,8 +110,10 @@ def niht_step(g, mask: np.ndarray, dx: np.ndarray, support: np.ndarray) -> float
 
 
 def ita_iteration(g, y: np.ndarray, mask: np.ndarray, x: np.ndarray, k: int,
-                  mu_mode: str = "fixed", mu: float = 1.0, kind: str = "soft"):
-    """One iteration of Algorithm 1 in the paper's order.  Returns (X^(i+1), stats)."""
+                  mu_mode: str = "fixed", mu: float = 1.0, kind: str = "soft",
+                  return_b: bool = False):
+    """One iteration of Algorithm 1 in the paper's order.  Returns (X^(i+1), stats),
+    plus b = X + mu Delta X when return_b."""
     r = mask * (y - csa.observe_G(g, x))                      # residue
     dx = csa.focus_M(g, r)                                    # MF on residue
     if mu_mode == "niht":
@@ -125,7 +127,7 @@ def ita_iteration(g, y: np.ndarray, mask: np.ndarray, x: np.ndarray, k: int,
     sigma = kth_largest_magnitude(b, k)                       # lambda_i mu_i
     x_new = threshold(b, sigma, kind)                         # thresholding
     st = IterStats(float(np.vdot(r, r).real), mu_i, sigma, int(np.count_nonzero(x_new)))
-    return x_new, st
+    return (x_new, st, b) if return_b else (x_new, st)
 
 
 def ita(g, y: np.ndarray, mask: np.ndarray, k: int, iters: int, mu_mode: str = "fixed",

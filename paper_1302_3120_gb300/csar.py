@@ -1,0 +1,266 @@
+"""Thin ctypes binding of libcsar (include/csar.h) with the same entry-point names.
+
+Argument marshalling only: every step of the imaging path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  The
+library must have been built (``paper_1302_3120_gb300.build.build()``); when it is
+missing the import of this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcsar.so")
+
+CSAR_OK = 0
+STATUS_NAMES = {0: "CSAR_OK", 1: "CSAR_E_INVALID", 2: "CSAR_E_UNSUPPORTED", 3: "CSAR_E_OOM",
+                4: "CSAR_E_CUDA", 5: "CSAR_E_TIMEOUT", 6: "CSAR_E_NONFINITE", 7: "CSAR_E_INTERNAL"}
+MU_MODES = {"fixed": 0, "niht": 1}
+THRESH = {"soft": 0, "half": 1}
+N_PASSES = 6
+PASS_NAMES = ("C1_sparse_fft", "R1_range_G", "C2_residue", "R2_range_M", "C3_select", "select_threshold")
+
+
+class CsarError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_az", ctypes.c_int32), ("n_rg", ctypes.c_int32),
+                ("wavelength", ctypes.c_double), ("velocity", ctypes.c_double),
+                ("r0", ctypes.c_double), ("prf", ctypes.c_double),
+                ("bandwidth", ctypes.c_double), ("pulse_len", ctypes.c_double),
+                ("fs", ctypes.c_double), ("antenna_len", ctypes.c_double),
+                ("c", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("iters", ctypes.c_int32), ("mu_mode", ctypes.c_int32),
+                ("mu", ctypes.c_float), ("thresh", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("resid_sq", ctypes.POINTER(ctypes.c_double)),
+                ("mu", ctypes.POINTER(ctypes.c_float)),
+                ("sigma", ctypes.POINTER(ctypes.c_float)),
+                ("nnz", ctypes.POINTER(ctypes.c_int64))]
+
+
+EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
+           "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
+           "csar_last_error", "csar_version")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcsar is not built ({LIB_PATH} missing); run "
+                          "paper_1302_3120_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+    lib.csar_plan_create.argtypes = [ctypes.POINTER(Params), u32, ctypes.POINTER(vp)]
+    lib.csar_plan_destroy.argtypes = [vp]
+    lib.csar_G.argtypes = [vp, vp, vp, vp]
+    lib.csar_M.argtypes = [vp, vp, vp, vp]
+    lib.csar_ita_step.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), vp, vp]
+    lib.csar_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
+    lib.csar_solve_host.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(Stats), vp]
+    lib.csar_solve_profile.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts),
+                                       ctypes.POINTER(ctypes.c_float), i32, vp]
+    lib.csar_plan_check.argtypes = [vp]
+    lib.csar_last_error.restype = ctypes.c_char_p
+    lib.csar_version.restype = i32
+    for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
+                 "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(st: int, where: str) -> None:
+    if st != CSAR_OK:
+        raise CsarError(st, where, lib.csar_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, n: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise TypeError(f"{name}: need contiguous {dtype} with {n} elements, got {t.dtype} "
+                        f"{tuple(t.shape)}")
+
+
+def params_of(g) -> Params:
+    """csar_params from any object with the system-parameter attributes."""
+    return Params(int(g.n_az), int(g.n_rg), float(g.wavelength), float(g.velocity), float(g.r0),
+                  float(g.prf), float(g.bandwidth), float(g.pulse_len), float(g.fs),
+                  float(getattr(g, "antenna_len", 0.0)), float(getattr(g, "c", 0.0)))
+
+
+class Plan:
+    """Owns a csar_plan handle (destroyed with the object)."""
+
+    def __init__(self, handle: int, n_az: int, n_rg: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n_az, self.n_rg = n_az, n_rg
+        self.n = n_az * n_rg
+
+    def close(self) -> None:
+        if self.handle:
+            lib.csar_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def csar_plan_create(geometry, flags: int = 0) -> Plan:
+    p = params_of(geometry)
+    h = ctypes.c_void_p()
+    _check(lib.csar_plan_create(ctypes.byref(p), flags, ctypes.byref(h)), "csar_plan_create")
+    return Plan(h.value, p.n_az, p.n_rg)
+
+
+def csar_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def _opts(K, iters, mu_mode, mu, thresh) -> Opts:
+    return Opts(int(K), int(iters), MU_MODES[mu_mode] if isinstance(mu_mode, str) else int(mu_mode),
+                float(mu), THRESH[thresh] if isinstance(thresh, str) else int(thresh))
+
+
+def csar_G(plan: Plan, x, y=None, stream=None):
+    """y = G(x) on [n_az, n_rg] complex64 CUDA tensors (y may be x)."""
+    import torch
+    _need(x, torch.complex64, plan.n, "x")
+    y = torch.empty_like(x) if y is None else y
+    _need(y, torch.complex64, plan.n, "y")
+    _check(lib.csar_G(plan.handle, _ptr(x), _ptr(y), _stream(stream)), "csar_G")
+    return y
+
+
+def csar_M(plan: Plan, y, x=None, stream=None):
+    """x = M(y) = G^H(y) on [n_az, n_rg] complex64 CUDA tensors (x may be y)."""
+    import torch
+    _need(y, torch.complex64, plan.n, "y")
+    x = torch.empty_like(y) if x is None else x
+    _need(x, torch.complex64, plan.n, "x")
+    _check(lib.csar_M(plan.handle, _ptr(y), _ptr(x), _stream(stream)), "csar_M")
+    return x
+
+
+def csar_ita_step(plan: Plan, Y, mask_bits, X, K: int, mu_mode="fixed", mu: float = 1.0,
+                  thresh="soft", sigma=None, stream=None):
+    """One ITA iteration in place on X (complex64 CUDA); mask_bits: int32 CUDA tensor
+    of n/32 packed words.  sigma: optional float32 CUDA tensor of 1 element."""
+    import torch
+    _need(Y, torch.complex64, plan.n, "Y")
+    _need(X, torch.complex64, plan.n, "X")
+    _need(mask_bits, torch.int32, plan.n // 32, "mask_bits")
+    o = _opts(K, 1, mu_mode, mu, thresh)
+    sp = ctypes.c_void_p(None) if sigma is None else _ptr(sigma)
+    _check(lib.csar_ita_step(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(X), ctypes.byref(o), sp,
+                             _stream(stream)), "csar_ita_step")
+    return X
+
+
+def _stats_struct(iters: int):
+    arrs = {"resid_sq": np.zeros(iters, np.float64), "mu": np.zeros(iters, np.float32),
+            "sigma": np.zeros(iters, np.float32), "nnz": np.zeros(iters, np.int64)}
+    st = Stats(arrs["resid_sq"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+               arrs["mu"].ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+               arrs["sigma"].ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+               arrs["nnz"].ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return st, arrs
+
+
+def csar_solve(plan: Plan, Y, mask_bits, K: int, iters: int, mu_mode="fixed", mu: float = 1.0,
+               thresh="soft", X=None, stats: bool = False, stream=None):
+    """Algorithm 1 from X = 0 for `iters` iterations; returns X (and the per-iteration
+    statistics dict when stats=True, which synchronises the stream)."""
+    import torch
+    _need(Y, torch.complex64, plan.n, "Y")
+    _need(mask_bits, torch.int32, plan.n // 32, "mask_bits")
+    X = torch.empty_like(Y) if X is None else X
+    _need(X, torch.complex64, plan.n, "X")
+    o = _opts(K, iters, mu_mode, mu, thresh)
+    st, arrs = _stats_struct(max(iters, 1)) if stats else (None, None)
+    _check(lib.csar_solve(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(X), ctypes.byref(o),
+                          ctypes.byref(st) if st is not None else None, _stream(stream)),
+           "csar_solve")
+    return (X, arrs) if stats else X
+
+
+def csar_solve_host(plan: Plan, Y: np.ndarray, mask_bits: np.ndarray, K: int, iters: int,
+                    mu_mode="fixed", mu: float = 1.0, thresh="soft", X: np.ndarray | None = None,
+                    stats: bool = False, stream=None):
+    """csar_solve from host numpy buffers (complex64 Y, uint32 mask words); returns X."""
+    Y = np.ascontiguousarray(Y, dtype=np.complex64)
+    mask_bits = np.ascontiguousarray(mask_bits, dtype=np.uint32)
+    if Y.size != plan.n or mask_bits.size != plan.n // 32:
+        raise ValueError("Y / mask_bits size does not match the plan")
+    if X is None:
+        X = np.empty(plan.n, dtype=np.complex64)
+    o = _opts(K, iters, mu_mode, mu, thresh)
+    st, arrs = _stats_struct(max(iters, 1)) if stats else (None, None)
+    _check(lib.csar_solve_host(plan.handle, ctypes.c_void_p(Y.ctypes.data),
+                               ctypes.c_void_p(mask_bits.ctypes.data), ctypes.c_void_p(X.ctypes.data),
+                               ctypes.byref(o), ctypes.byref(st) if st is not None else None,
+                               _stream(stream)), "csar_solve_host")
+    return (X, arrs) if stats else X
+
+
+def csar_solve_profile(plan: Plan, Y, mask_bits, K: int, iters: int, mu_mode="fixed",
+                       mu: float = 1.0, thresh="soft", X=None, stream=None):
+    """csar_solve with CUDA events around every pass; returns (X, {pass: ms summed})."""
+    import torch
+    X = torch.empty_like(Y) if X is None else X
+    o = _opts(K, iters, mu_mode, mu, thresh)
+    ms = (ctypes.c_float * N_PASSES)()
+    _check(lib.csar_solve_profile(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(X), ctypes.byref(o),
+                                  ms, N_PASSES, _stream(stream)), "csar_solve_profile")
+    return X, dict(zip(PASS_NAMES, [float(v) for v in ms]))
+
+
+def csar_plan_check(plan: Plan) -> None:
+    _check(lib.csar_plan_check(plan.handle), "csar_plan_check")
+
+
+def csar_version() -> int:
+    return int(lib.csar_version())
+
+
+def pack_mask_torch(mask_bool):
+    """Pack a boolean [n_az, n_rg] torch mask into int32 words (bit j of word w is
+    element 32 w + j) on the mask's device."""
+    import torch
+    flat = mask_bool.reshape(-1, 32).to(torch.int64)
+    weights = (torch.ones(32, dtype=torch.int64, device=flat.device) << torch.arange(
+        32, device=flat.device))
+    words = (flat * weights).sum(dim=1)
+    words = torch.where(words >= 2 ** 31, words - 2 ** 32, words)
+    return words.to(torch.int32)

@@ -1,0 +1,749 @@
+// csar_plan.cu — host side of libcsar: the C ABI declared in include/csar.h.
+//
+// Plan creation evaluates the chirp-scaling phase functions' coefficients in FP64
+// (one quadratic polynomial per azimuth-frequency row and phase, Section III-D with
+// the textbook CSA functions), the FFT twiddles, and allocates the workspace.  The
+// ITA iteration (Algorithm 1) is a fixed sequence of kernels (column pass, row
+// pass, column pass, row pass, column pass, selection, threshold) captured once per
+// ping-pong parity into a CUDA graph; data-dependent choices (the exact re-pass of
+// the selection, the NIHT branch) are taken on the device by kernels that return
+// early, so one graph serves every iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/csar.h"
+#include "fft.cuh"
+#include "internal.h"
+
+using namespace csar;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+csar_status fail(csar_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+csar_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? CSAR_E_OOM : CSAR_E_CUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+void split(double v, float* hi, float* lo) {
+  *hi = (float)v;
+  *lo = (float)(v - (double)*hi);
+}
+
+PhaseCoef make_coef(double a, double b, double c, double sign) {
+  PhaseCoef p;
+  a *= sign;
+  b *= sign;
+  c *= sign;
+  a -= std::nearbyint(a);
+  split(a, &p.a_hi, &p.a_lo);
+  split(b, &p.b_hi, &p.b_lo);
+  split(c, &p.c_hi, &p.c_lo);
+  return p;
+}
+
+struct Buffers {
+  float2* z = nullptr;             // n: pass-to-pass array
+  uint32_t* off[2] = {nullptr, nullptr};
+  uint32_t* idx[2] = {nullptr, nullptr};
+  float2* val[2] = {nullptr, nullptr};
+  float2* dx = nullptr;            // Delta X on the support
+  uint32_t* cand_idx = nullptr;
+  float2* cand_val = nullptr;
+  uint32_t cand_cap = 0;
+  uint32_t* hist = nullptr;
+  uint32_t* hist2 = nullptr;
+  uint32_t* tile_cnt = nullptr;
+  uint32_t* tile_cur = nullptr;
+  float* partial = nullptr;
+  float* partial_norm = nullptr;
+  uint32_t* mask_t = nullptr;      // sampling mask in column-pass order
+  Ctl* ctl = nullptr;
+  IterStat* stats = nullptr;
+  int stats_cap = 0;
+  // host-buffer entry point
+  float2* hY = nullptr;
+  uint32_t* hMask = nullptr;
+  float2* hX = nullptr;
+};
+
+struct GraphKey {
+  const void* y = nullptr;
+  const void* mask = nullptr;
+  int64_t K = -1;
+  int mu_mode = -1, thresh = -1;
+  float mu = 0.f;
+  uint32_t cand_cap = 0;
+  IterStat* stats = nullptr;
+  bool operator==(const GraphKey& o) const {
+    return y == o.y && mask == o.mask && K == o.K && mu_mode == o.mu_mode && thresh == o.thresh &&
+           mu == o.mu && cand_cap == o.cand_cap && stats == o.stats;
+  }
+};
+
+}  // namespace
+
+struct csar_plan_s {
+  csar_params p{};
+  int dev = 0;
+  int na = 0, nr = 0;
+  int64_t n = 0;
+  int col_tile = 0, n_tiles = 0;
+  RowCoef* coef_g = nullptr;
+  RowCoef* coef_m = nullptr;
+  float2* tw = nullptr;
+  Buffers b;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  GraphKey key[2];
+  bool use_graphs = true;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+csar_status validate(const csar_params* p) {
+  if (!p) return fail(CSAR_E_INVALID, "params is NULL");
+  if (!pow2_in(p->n_az, 16, 8192) || !pow2_in(p->n_rg, 16, 8192))
+    return fail(CSAR_E_INVALID, "n_az=%d n_rg=%d: each must be a power of two in [16, 8192]",
+                p->n_az, p->n_rg);
+  const double vals[] = {p->wavelength, p->velocity, p->r0, p->prf, p->bandwidth, p->pulse_len, p->fs};
+  const char* names[] = {"wavelength", "velocity", "r0", "prf", "bandwidth", "pulse_len", "fs"};
+  for (int i = 0; i < 7; ++i)
+    if (!(vals[i] > 0.0) || !std::isfinite(vals[i]))
+      return fail(CSAR_E_INVALID, "%s must be finite and > 0", names[i]);
+  if (p->c < 0.0 || !std::isfinite(p->c)) return fail(CSAR_E_INVALID, "c must be >= 0");
+  return CSAR_OK;
+}
+
+// Per-row coefficients (cycles) of the three chirp-scaling phases; see phase.cuh.
+//   H1 = exp{j pi K_m (1/D - 1)(tau - 2 R_ref/(c D))^2},      tau - 2R_ref/c = j'/fs
+//   H2 = exp{j pi (D/K_m) f_tau^2} exp{j 4 pi f_tau R_ref (1/D - 1)/c},  f_tau = m fs/N_r
+//   H3 = exp{j 4 pi R0 f0 D/c} exp{-j 4 pi (K_m/c^2)(1 - D)((R0 - R_ref)/D)^2},
+//        R0 = R_ref + j' c/(2 fs)
+csar_status build_coefs(const csar_params& p, std::vector<RowCoef>& g, std::vector<RowCoef>& m) {
+  const double c = p.c > 0.0 ? p.c : 299792458.0;
+  const double f0 = c / p.wavelength;
+  const double kr = p.bandwidth / p.pulse_len;
+  const double rref = p.r0;
+  const double fs = p.fs;
+  const int na = p.n_az, nr = p.n_rg;
+  const double jmax = nr / 2.0;  // |j'|, |m| <= N_r/2
+  const double lim = 4194304.0;  // 2^22
+  g.resize(na);
+  m.resize(na);
+  for (int k = 0; k < na; ++k) {
+    const int ks = k < na / 2 ? k : k - na;
+    const double fe = ks * p.prf / na;
+    const double x = c * fe / (2.0 * p.velocity * f0);
+    if (!(x * x < 1.0))
+      return fail(CSAR_E_UNSUPPORTED, "Doppler frequency %.6g Hz exceeds 2V/lambda", fe);
+    const double d = std::sqrt(1.0 - x * x);
+    const double km = kr / (1.0 - kr * c * rref * fe * fe / (2.0 * p.velocity * p.velocity * f0 * f0 * f0 * d * d * d));
+    // H1
+    const double a1 = 0.5 * km * (1.0 / d - 1.0);
+    const double del = (2.0 * rref / c) * (1.0 / d - 1.0);
+    const double h1c = a1 / (fs * fs), h1b = -2.0 * a1 * del / fs, h1a = a1 * del * del;
+    // H2
+    const double df = fs / nr;
+    const double h2c = 0.5 * (d / km) * df * df, h2b = 2.0 * df * rref * (1.0 / d - 1.0) / c, h2a = 0.0;
+    // H3
+    const double h3a = 2.0 * f0 * d * rref / c, h3b = f0 * d / fs;
+    const double h3c = -km * (1.0 - d) / (2.0 * d * d * fs * fs);
+    const double bs[] = {h1b, h2b, h3b}, cs[] = {h1c, h2c, h3c};
+    for (int i = 0; i < 3; ++i)
+      if (std::fabs(bs[i]) * jmax >= lim || std::fabs(cs[i]) * jmax * jmax >= lim || !std::isfinite(bs[i]) ||
+          !std::isfinite(cs[i]))
+        return fail(CSAR_E_UNSUPPORTED,
+                    "phase polynomial too large for on-the-fly evaluation (row %d, phase H%d)", k, i + 1);
+    m[k].pro = make_coef(h1a, h1b, h1c, 1.0);
+    m[k].mid = make_coef(h2a, h2b, h2c, 1.0);
+    m[k].epi = make_coef(h3a, h3b, h3c, 1.0);
+    g[k].pro = make_coef(h3a, h3b, h3c, -1.0);
+    g[k].mid = make_coef(h2a, h2b, h2c, -1.0);
+    g[k].epi = make_coef(h1a, h1b, h1c, -1.0);
+  }
+  return CSAR_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+}
+
+void free_buffers(Buffers& b) {
+  void* ptrs[] = {b.z, b.off[0], b.off[1], b.idx[0], b.idx[1], b.val[0], b.val[1], b.dx, b.cand_idx,
+                  b.cand_val, b.hist, b.hist2, b.tile_cnt, b.tile_cur, b.partial, b.partial_norm, b.mask_t, b.ctl,
+                  b.stats, b.hY, b.hMask, b.hX};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  b = Buffers();
+}
+
+void drop_graphs(csar_plan plan) {
+  for (int i = 0; i < 2; ++i) {
+    if (plan->exec[i]) cudaGraphExecDestroy(plan->exec[i]);
+    plan->exec[i] = nullptr;
+    plan->key[i] = GraphKey();
+  }
+}
+
+// Candidate capacity for sparsity K (grown on demand, never during capture).
+csar_status ensure_capacity(csar_plan plan, int64_t K, int iters) {
+  Buffers& b = plan->b;
+  const int64_t want64 = std::min<int64_t>(plan->n, std::max<int64_t>(int64_t(1) << 20, 8 * (K + 1)));
+  const uint32_t want = (uint32_t)want64;
+  if (b.cand_cap < want) {
+    drop_graphs(plan);
+    if (b.cand_idx) cudaFree(b.cand_idx);
+    if (b.cand_val) cudaFree(b.cand_val);
+    b.cand_idx = nullptr;
+    b.cand_val = nullptr;
+    b.cand_cap = 0;
+    CK(dalloc(&b.cand_idx, want));
+    CK(dalloc(&b.cand_val, want));
+    b.cand_cap = want;
+  }
+  if (b.stats_cap < iters) {
+    drop_graphs(plan);
+    if (b.stats) cudaFree(b.stats);
+    b.stats = nullptr;
+    b.stats_cap = 0;
+    const int cap = std::max(iters, 256);
+    CK(dalloc(&b.stats, cap));
+    b.stats_cap = cap;
+  }
+  return CSAR_OK;
+}
+
+ColArgs col_args(csar_plan plan) {
+  ColArgs a{};
+  a.tw = plan->tw;
+  a.nr = plan->nr;
+  a.ctl = plan->b.ctl;
+  a.hist = plan->b.hist;
+  a.cand_idx = plan->b.cand_idx;
+  a.cand_val = plan->b.cand_val;
+  a.cand_cap = plan->b.cand_cap;
+  a.partial = plan->b.partial;
+  a.xs_dx = plan->b.dx;
+  a.scale = 1.0f / (float)plan->na;
+  return a;
+}
+
+RowArgs row_args(csar_plan plan, float2* data, const RowCoef* coef) {
+  RowArgs r{};
+  r.data = data;
+  r.coef = coef;
+  r.tw = plan->tw;
+  r.n_rows = plan->na;
+  r.scale = 1.0f / (float)plan->nr;
+  return r;
+}
+
+SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
+  const Buffers& b = plan->b;
+  const int nxt = 1 - cur;
+  SelArgs s{};
+  s.ctl = b.ctl;
+  s.hist = b.hist;
+  s.hist_mut = b.hist;
+  s.hist2 = b.hist2;
+  s.xs_idx = b.idx[cur];
+  s.xs_val = b.val[cur];
+  s.xs_dx = b.dx;
+  s.cand_idx = b.cand_idx;
+  s.cand_val = b.cand_val;
+  s.cand_cap = b.cand_cap;
+  s.tile_cnt = b.tile_cnt;
+  s.tile_cur = b.tile_cur;
+  s.xo_off = b.off[nxt];
+  s.xo_idx = b.idx[nxt];
+  s.xo_val = b.val[nxt];
+  s.partial = b.partial;
+  s.partial_norm = b.partial_norm;
+  s.n_partial = plan->n_tiles;
+  s.stats = b.stats;
+  s.K = o.K;
+  s.n = plan->n;
+  s.nr = plan->nr;
+  s.col_tile = plan->col_tile;
+  s.n_tiles = plan->n_tiles;
+  s.thresh = o.thresh;
+  s.mu_mode = o.mu_mode;
+  s.mu_fixed = o.mu;
+  return s;
+}
+
+#define LK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+// One ITA iteration reading the sparse iterate in list `cur` and writing list 1-cur.
+// Optional per-pass events (profiling): ev[0..kPasses].
+constexpr int kPasses = 6;  // C1, R1, C2, R2, C3, selection+threshold
+cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const csar_opts& o,
+                              cudaStream_t s, cudaEvent_t* ev) {
+  Buffers& b = plan->b;
+  const uint32_t* mask = b.mask_t;
+  const int na = plan->na, nr = plan->nr, nt = plan->n_tiles;
+  const int nxt = 1 - cur;
+  auto mark = [&](int i) -> cudaError_t { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+  ColArgs c = col_args(plan);
+  c.xs_off = b.off[cur];
+  c.xs_idx = b.idx[cur];
+  c.xs_val = b.val[cur];
+  LK(mark(0));
+  // G(X): F_a of the sparse iterate, range pass with conj(H3), conj(H2), conj(H1)
+  c.out = b.z;
+  LK(launch_col(na, COL_SPARSE_FWD, c, nt, s));
+  LK(mark(1));
+  LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
+  LK(mark(2));
+  // residue r = S.(Y - G(X)) and F_a r
+  c.in = b.z;
+  c.out = b.z;
+  c.y = y;
+  c.mask = mask;
+  LK(launch_col(na, COL_RESID, c, nt, s));
+  LK(mark(3));
+  // M(r): range pass with H1, H2, H3
+  LK(launch_row(nr, row_args(plan, b.z, plan->coef_m), s));
+  LK(mark(4));
+  // Delta X = F_a^-1: support values, histogram, candidates
+  LK(launch_col(na, COL_SELECT, c, nt, s));
+  LK(mark(5));
+  SelArgs sa = sel_args(plan, cur, o);
+  LK(launch_sel_check(sa, s));
+  LK(launch_col(na, COL_REPASS, c, nt, s));
+  if (o.mu_mode == CSAR_MU_NIHT) {
+    // NIHT step on Gamma = supp X^(i) (skipped on the device when the support is empty)
+    ColArgs g = col_args(plan);
+    g.gate = &b.ctl->niht_first;
+    g.gate_val = 0u;
+    g.xs_off = b.off[cur];
+    g.xs_idx = b.idx[cur];
+    g.xs_val = b.dx;
+    g.out = b.z;
+    LK(launch_col(na, COL_SPARSE_FWD, g, nt, s));
+    RowArgs r = row_args(plan, b.z, plan->coef_g);
+    r.gate = g.gate;
+    r.gate_val = 0u;
+    LK(launch_row(nr, r, s));
+    g.in = b.z;
+    g.mask = mask;
+    g.partial = b.partial_norm;
+    LK(launch_col(na, COL_NORM, g, nt, s));
+    LK(launch_niht_mu_mode(sa, 0, s));
+  }
+  for (int lev = 0; lev < 3; ++lev) {
+    LK(launch_sel_round(sa, lev, s));
+    LK(launch_sel_pick(sa, lev, s));
+  }
+  LK(launch_thr_count(sa, s));
+  LK(launch_thr_scan(sa, s));
+  LK(launch_thr_scatter_mode(sa, o.mu_mode == CSAR_MU_NIHT ? 1 : 0, s));
+  if (o.mu_mode == CSAR_MU_NIHT) {
+    // first iteration: Gamma = the top-K list just written (raw Delta X values)
+    ColArgs g = col_args(plan);
+    g.gate = &b.ctl->niht_first;
+    g.gate_val = 1u;
+    g.xs_off = b.off[nxt];
+    g.xs_idx = b.idx[nxt];
+    g.xs_val = b.val[nxt];
+    g.out = b.z;
+    LK(launch_col(na, COL_SPARSE_FWD, g, nt, s));
+    RowArgs r = row_args(plan, b.z, plan->coef_g);
+    r.gate = g.gate;
+    r.gate_val = 1u;
+    LK(launch_row(nr, r, s));
+    g.in = b.z;
+    g.mask = mask;
+    g.partial = b.partial_norm;
+    LK(launch_col(na, COL_NORM, g, nt, s));
+    LK(launch_niht_mu_mode(sa, 1, s));
+  }
+  LK(launch_sel_finish(sa, s));
+  LK(mark(6));
+  return cudaSuccess;
+}
+
+__global__ void k_ctl_init(Ctl* c, uint32_t nx_from_list, const uint32_t* off0, int n_tiles) {
+  Ctl z{};
+  z.cut_key = kNoCandidates;
+  z.nx = nx_from_list ? off0[n_tiles] : 0u;
+  *c = z;
+}
+
+csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
+  if (!o) return fail(CSAR_E_INVALID, "opts is NULL");
+  if (o->K < 0) return fail(CSAR_E_INVALID, "K must be >= 0");
+  if (need_iters && o->iters < 0) return fail(CSAR_E_INVALID, "iters must be >= 0");
+  if (o->mu_mode != CSAR_MU_FIXED && o->mu_mode != CSAR_MU_NIHT)
+    return fail(CSAR_E_INVALID, "mu_mode must be CSAR_MU_FIXED or CSAR_MU_NIHT");
+  if (o->mu_mode == CSAR_MU_FIXED && !(o->mu > 0.f && std::isfinite(o->mu)))
+    return fail(CSAR_E_INVALID, "mu must be finite and > 0");
+  if (o->thresh != CSAR_THRESH_SOFT && o->thresh != CSAR_THRESH_HALF)
+    return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT or CSAR_THRESH_HALF");
+  (void)plan;
+  return CSAR_OK;
+}
+
+csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!in || !out) return fail(CSAR_E_INVALID, "null data pointer");
+  const size_t bytes = (size_t)plan->n * sizeof(float2);
+  const char* ib = (const char*)in;
+  const char* ob = (const char*)out;
+  if (ib != ob && ib < ob + bytes && ob < ib + bytes)
+    return fail(CSAR_E_INVALID, "input and output overlap without being identical");
+  DeviceGuard dg(plan->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  ColArgs c = col_args(plan);
+  c.in = (const float2*)in;
+  c.out = (float2*)out;
+  cudaError_t e = launch_col(plan->na, COL_FWD, c, plan->n_tiles, s);
+  if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), s);
+  c.in = (const float2*)out;
+  if (e == cudaSuccess) e = launch_col(plan->na, COL_INV, c, plan->n_tiles, s);
+  if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G" : "csar_M");
+  return CSAR_OK;
+}
+
+csar_status latched(csar_plan plan) {
+  Ctl c;
+  CK(cudaMemcpy(&c, plan->b.ctl, sizeof c, cudaMemcpyDeviceToHost));
+  if (c.err) {
+    const uint32_t zero = 0;
+    CK(cudaMemcpy(&plan->b.ctl->err, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    if (c.err & kErrNonfinite) return fail(CSAR_E_NONFINITE, "non-finite value in the echo or iterate");
+    if (c.err & kErrCapacity)
+      return fail(CSAR_E_INTERNAL, "selection candidate capacity exceeded (degenerate magnitudes)");
+    return fail(CSAR_E_INTERNAL, "device error bits 0x%x", c.err);
+  }
+  return CSAR_OK;
+}
+
+// Run `iters` iterations starting from list 0 (already initialised); returns the
+// parity holding the result.
+csar_status run_iterations(csar_plan plan, const float2* y, const uint32_t* mask, const csar_opts& o,
+                           int iters, cudaStream_t s, int* result_parity) {
+  int cur = 0;
+  for (int i = 0; i < iters; ++i) {
+    if (plan->use_graphs) {
+      GraphKey k;
+      k.y = y;
+      k.mask = mask;
+      k.K = o.K;
+      k.mu_mode = o.mu_mode;
+      k.thresh = o.thresh;
+      k.mu = o.mu;
+      k.cand_cap = plan->b.cand_cap;
+      k.stats = plan->b.stats;
+      if (!plan->exec[cur] || !(plan->key[cur] == k)) {
+        if (plan->exec[cur]) cudaGraphExecDestroy(plan->exec[cur]);
+        plan->exec[cur] = nullptr;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_iteration(plan, y, cur, o, plan->cap_stream, nullptr);
+        cudaError_t e2 = cudaStreamEndCapture(plan->cap_stream, &g);
+        if (e != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          return cuda_fail(e, "capture of the ITA iteration");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        cudaError_t e3 = cudaGraphInstantiate(&plan->exec[cur], g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) return cuda_fail(e3, "cudaGraphInstantiate");
+        plan->key[cur] = k;
+      }
+      CK(cudaGraphLaunch(plan->exec[cur], s));
+    } else {
+      cudaError_t e = enqueue_iteration(plan, y, cur, o, s, nullptr);
+      if (e != cudaSuccess) return cuda_fail(e, "ITA iteration");
+    }
+    cur = 1 - cur;
+  }
+  *result_parity = cur;
+  return CSAR_OK;
+}
+
+csar_status solve_impl(csar_plan plan, const void* Y, const uint32_t* mask, void* X, const csar_opts* o,
+                       const csar_stats* stats, cudaStream_t s) {
+  if (csar_status st = check_opts(plan, o, true)) return st;
+  if (!Y || !mask || !X) return fail(CSAR_E_INVALID, "null data pointer");
+  if (csar_status st = ensure_capacity(plan, o->K, o->iters)) return st;
+  Buffers& b = plan->b;
+  CK(launch_mask_transpose(plan->na, plan->nr, mask, b.mask_t, s));
+  // X^(0) = 0: empty list 0, fresh control block
+  CK(cudaMemsetAsync(b.off[0], 0, (plan->n_tiles + 1) * sizeof(uint32_t), s));
+  k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 0u, b.off[0], plan->n_tiles);
+  CK(cudaGetLastError());
+  int par = 0;
+  if (csar_status st = run_iterations(plan, (const float2*)Y, mask, *o, o->iters, s, &par)) return st;
+  CK(cudaMemsetAsync(X, 0, (size_t)plan->n * sizeof(float2), s));
+  CK(launch_list_to_dense(b.off[par], b.idx[par], b.val[par], plan->n_tiles, (float2*)X, s));
+  if (stats && o->iters > 0) {
+    std::vector<IterStat> h(o->iters);
+    CK(cudaMemcpyAsync(h.data(), b.stats, o->iters * sizeof(IterStat), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < o->iters; ++i) {
+      if (stats->resid_sq) stats->resid_sq[i] = h[i].resid_sq;
+      if (stats->mu) stats->mu[i] = h[i].mu;
+      if (stats->sigma) stats->sigma[i] = h[i].sigma;
+      if (stats->nnz) stats->nnz[i] = h[i].nnz;
+    }
+    return latched(plan);
+  }
+  return CSAR_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* csar_last_error(void) { return g_last_error.c_str(); }
+
+int32_t csar_version(void) { return 10000; }
+
+csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
+  if (!out) return fail(CSAR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (flags != 0) return fail(CSAR_E_INVALID, "flags must be 0");
+  if (csar_status st = validate(params)) return st;
+  std::vector<RowCoef> cg, cm;
+  if (csar_status st = build_coefs(*params, cg, cm)) return st;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  csar_plan plan = new csar_plan_s();
+  plan->p = *params;
+  plan->dev = dev;
+  plan->na = params->n_az;
+  plan->nr = params->n_rg;
+  plan->n = (int64_t)plan->na * plan->nr;
+  plan->col_tile = col_w(plan->na);
+  plan->n_tiles = plan->nr / plan->col_tile;
+  const char* ng = std::getenv("CSAR_NO_GRAPH");
+  plan->use_graphs = !(ng && ng[0] == '1');
+  auto bail = [&](csar_status st) {
+    csar_plan_destroy(plan);
+    return st;
+  };
+  cudaError_t e;
+#define PK(call)                                      \
+  if ((e = (call)) != cudaSuccess) {                  \
+    csar_status st_ = cuda_fail(e, #call);            \
+    return bail(st_);                                 \
+  }
+  PK(col_set_attributes(plan->na));
+  PK(row_set_attributes(plan->nr));
+  PK(dalloc(&plan->coef_g, plan->na));
+  PK(dalloc(&plan->coef_m, plan->na));
+  PK(cudaMemcpy(plan->coef_g, cg.data(), cg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
+  PK(cudaMemcpy(plan->coef_m, cm.data(), cm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
+  {
+    std::vector<float2> tw(kTwLo + kTwHi);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < kTwLo; ++m) {
+      const double a = two_pi * m / kTwN;
+      tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    for (int h = 0; h < kTwHi; ++h) {
+      const double a = two_pi * (double)(h * kTwLo) / kTwN;
+      tw[kTwLo + h] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    PK(dalloc(&plan->tw, tw.size()));
+    PK(cudaMemcpy(plan->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+  Buffers& b = plan->b;
+  const size_t n = (size_t)plan->n;
+  const int nt = plan->n_tiles;
+  PK(dalloc(&b.z, n));
+  for (int i = 0; i < 2; ++i) {
+    PK(dalloc(&b.off[i], nt + 1));
+    PK(dalloc(&b.idx[i], n));
+    PK(dalloc(&b.val[i], n));
+    PK(cudaMemset(b.off[i], 0, (nt + 1) * sizeof(uint32_t)));
+  }
+  PK(dalloc(&b.dx, n));
+  PK(dalloc(&b.hist, kHistBins));
+  PK(dalloc(&b.hist2, kHistBins));
+  PK(dalloc(&b.tile_cnt, nt));
+  PK(dalloc(&b.tile_cur, nt));
+  PK(dalloc(&b.partial, nt));
+  PK(dalloc(&b.partial_norm, nt));
+  PK(dalloc(&b.mask_t, (size_t)plan->nr * (plan->na / regs_for(plan->na))));
+  PK(dalloc(&b.ctl, 1));
+  PK(cudaMemset(b.hist, 0, kHistBins * sizeof(uint32_t)));
+  PK(cudaMemset(b.hist2, 0, kHistBins * sizeof(uint32_t)));
+  PK(cudaMemset(b.tile_cnt, 0, nt * sizeof(uint32_t)));
+  PK(cudaMemset(b.ctl, 0, sizeof(Ctl)));
+  PK(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+#undef PK
+  *out = plan;
+  return CSAR_OK;
+}
+
+csar_status csar_plan_destroy(csar_plan plan) {
+  if (!plan) return CSAR_OK;
+  DeviceGuard dg(plan->dev);
+  cudaDeviceSynchronize();
+  drop_graphs(plan);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  free_buffers(plan->b);
+  if (plan->coef_g) cudaFree(plan->coef_g);
+  if (plan->coef_m) cudaFree(plan->coef_m);
+  if (plan->tw) cudaFree(plan->tw);
+  delete plan;
+  return CSAR_OK;
+}
+
+csar_status csar_G(csar_plan plan, const void* x_dev, void* y_dev, void* stream) {
+  return run_op(plan, x_dev, y_dev, true, stream);
+}
+
+csar_status csar_M(csar_plan plan, const void* y_dev, void* x_dev, void* stream) {
+  return run_op(plan, y_dev, x_dev, false, stream);
+}
+
+csar_status csar_ita_step(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
+                          const csar_opts* opts, float* sigma_dev, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (csar_status st = check_opts(plan, opts, false)) return st;
+  if (!Y_dev || !mask_dev || !X_dev) return fail(CSAR_E_INVALID, "null data pointer");
+  DeviceGuard dg(plan->dev);
+  if (csar_status st = ensure_capacity(plan, opts->K, 1)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Buffers& b = plan->b;
+  const float2* X = (const float2*)X_dev;
+  // dense X -> bucketed list 0
+  CK(launch_dense_count(X, plan->na, plan->nr, plan->col_tile, b.tile_cnt, s));
+  CK(launch_dense_scan(b.tile_cnt, b.tile_cur, b.off[0], plan->n_tiles, nullptr, s));
+  CK(launch_dense_scatter(X, plan->na, plan->nr, plan->col_tile, b.tile_cur, b.idx[0], b.val[0], s));
+  k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 1u, b.off[0], plan->n_tiles);
+  CK(cudaGetLastError());
+  CK(launch_mask_transpose(plan->na, plan->nr, mask_dev, b.mask_t, s));
+  cudaError_t e = enqueue_iteration(plan, (const float2*)Y_dev, 0, *opts, s, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "csar_ita_step");
+  CK(cudaMemsetAsync(X_dev, 0, (size_t)plan->n * sizeof(float2), s));
+  CK(launch_list_to_dense(b.off[1], b.idx[1], b.val[1], plan->n_tiles, (float2*)X_dev, s));
+  if (sigma_dev)
+    CK(cudaMemcpyAsync(sigma_dev, &b.ctl->sigma, sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return CSAR_OK;
+}
+
+csar_status csar_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
+                       const csar_opts* opts, const csar_stats* stats, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  DeviceGuard dg(plan->dev);
+  return solve_impl(plan, Y_dev, mask_dev, X_dev, opts, stats, (cudaStream_t)stream);
+}
+
+csar_status csar_solve_host(csar_plan plan, const void* Y_host, const uint32_t* mask_host, void* X_host,
+                            const csar_opts* opts, const csar_stats* stats, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!Y_host || !mask_host || !X_host) return fail(CSAR_E_INVALID, "null data pointer");
+  DeviceGuard dg(plan->dev);
+  Buffers& b = plan->b;
+  const size_t n = (size_t)plan->n;
+  if (!b.hY) {
+    CK(dalloc(&b.hY, n));
+    CK(dalloc(&b.hMask, n / 32));
+    CK(dalloc(&b.hX, n));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(b.hY, Y_host, n * sizeof(float2), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b.hMask, mask_host, n / 32 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+  if (csar_status st = solve_impl(plan, b.hY, b.hMask, b.hX, opts, stats, s)) return st;
+  CK(cudaMemcpyAsync(X_host, b.hX, n * sizeof(float2), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return latched(plan);
+}
+
+csar_status csar_plan_check(csar_plan plan) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  DeviceGuard dg(plan->dev);
+  CK(cudaDeviceSynchronize());
+  return latched(plan);
+}
+
+csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
+                               const csar_opts* opts, float* pass_ms, int32_t n_pass, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (csar_status st = check_opts(plan, opts, true)) return st;
+  if (!Y_dev || !mask_dev || !X_dev || !pass_ms || n_pass < kPasses)
+    return fail(CSAR_E_INVALID, "null pointer or n_pass < %d", kPasses);
+  DeviceGuard dg(plan->dev);
+  if (csar_status st = ensure_capacity(plan, opts->K, opts->iters)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Buffers& b = plan->b;
+  const int iters = opts->iters;
+  std::vector<cudaEvent_t> ev((size_t)(kPasses + 1) * std::max(iters, 1));
+  for (auto& x : ev) CK(cudaEventCreate(&x));
+  CK(launch_mask_transpose(plan->na, plan->nr, mask_dev, b.mask_t, s));
+  CK(cudaMemsetAsync(b.off[0], 0, (plan->n_tiles + 1) * sizeof(uint32_t), s));
+  k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 0u, b.off[0], plan->n_tiles);
+  int cur = 0;
+  for (int i = 0; i < iters; ++i) {
+    cudaError_t e = enqueue_iteration(plan, (const float2*)Y_dev, cur, *opts, s,
+                                      &ev[(size_t)i * (kPasses + 1)]);
+    if (e != cudaSuccess) return cuda_fail(e, "csar_solve_profile");
+    cur = 1 - cur;
+  }
+  CK(cudaMemsetAsync(X_dev, 0, (size_t)plan->n * sizeof(float2), s));
+  CK(launch_list_to_dense(b.off[cur], b.idx[cur], b.val[cur], plan->n_tiles, (float2*)X_dev, s));
+  CK(cudaStreamSynchronize(s));
+  for (int p = 0; p < kPasses; ++p) pass_ms[p] = 0.f;
+  for (int i = 0; i < iters; ++i)
+    for (int p = 0; p < kPasses; ++p) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[(size_t)i * (kPasses + 1) + p], ev[(size_t)i * (kPasses + 1) + p + 1]));
+      pass_ms[p] += ms;
+    }
+  for (auto& x : ev) cudaEventDestroy(x);
+  return latched(plan);
+}
+
+}  // extern "C"

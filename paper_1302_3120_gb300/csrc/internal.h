@@ -1,0 +1,159 @@
+// internal.h — types shared by the host driver and the kernels of libcsar.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+#include "phase.cuh"
+
+namespace csar {
+
+// ---------------------------------------------------------------- selection constants
+// Keys are the IEEE bit patterns of |b|^2 (non-negative floats order like uint32).
+constexpr uint32_t kHistBins = 4096;     // column-pass histogram: key >> 19 (bits 30..19)
+constexpr int kHistShift = 19;
+constexpr uint32_t kMinKey = 1u << 23;   // keys below this are 0 or subnormal |b|^2
+constexpr uint32_t kNoCandidates = 0xffffffffu;
+
+// Device-latched error bits (reported by csar_plan_check).
+enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u };
+
+// Column-pass modes.
+enum ColMode : int {
+  COL_FWD = 0,        // out = F_a in
+  COL_INV = 1,        // out = F_a^-1 in
+  COL_SPARSE_FWD = 2, // out = F_a (list scattered into a zero tile)
+  COL_RESID = 3,      // g = F_a^-1 in; r = S.(Y - g); out = F_a r; partial ||r||^2
+  COL_SELECT = 4,     // dx = F_a^-1 in; Delta X at the support; histogram; candidates
+  COL_REPASS = 5,     // COL_SELECT again with the exact cut, only if ctl->need_repass
+  COL_NORM = 6,       // g = F_a^-1 in; partial sum of S.|g|^2 (no store)
+};
+
+// Control block of one plan's iteration pipeline (device memory).
+struct Ctl {
+  uint32_t cut_key;      // candidate threshold on |Delta X|^2 bits
+  uint32_t cand_count;   // candidates appended (may exceed the capacity)
+  uint32_t need_repass;  // set by the check kernel
+  uint32_t err;          // latched error bits
+  uint32_t sel_prefix;   // radix select: key bits fixed so far
+  uint32_t sel_rank;     // radix select: rank (0-based, descending) within the prefix
+  uint32_t sigma2_key;   // key of the (K+1)-th largest |b|^2 (0: keep every nonzero)
+  uint32_t union_n;      // elements in the selection union
+  uint32_t nx;           // current sparse-iterate length
+  uint32_t nnz;          // new sparse-iterate length
+  uint32_t iter;         // iteration index (stats slot)
+  uint32_t niht_first;   // NIHT with an empty support: Gamma = top K of |Delta X|
+  float mu;              // step of the current iteration
+  float sigma;           // threshold of the current iteration
+  double niht_num;       // ||Delta X_Gamma||^2
+  double niht_den;       // ||S . G(Delta X_Gamma)||^2
+};
+
+// Per-iteration statistics (device).
+struct IterStat {
+  double resid_sq;
+  float mu;
+  float sigma;
+  uint32_t nnz;
+  uint32_t pad;
+};
+
+struct ColArgs {
+  const float2* in;
+  float2* out;
+  const float2* y;          // COL_RESID: echo
+  const uint32_t* mask;     // COL_RESID / COL_NORM: sampling mask in column-pass order
+                            // (launch_mask_transpose)
+  const uint32_t* xs_off;   // sparse iterate bucketed by column tile: offsets [tiles+1]
+  const uint32_t* xs_idx;   // flat indices row*nr+col
+  const float2* xs_val;     // values (COL_SPARSE_FWD reads these)
+  float2* xs_dx;            // COL_SELECT: Delta X at the support entries
+  uint32_t* hist;           // COL_SELECT: global histogram [kHistBins]
+  uint32_t* cand_idx;       // candidates (off-support, |Delta X|^2 >= cut)
+  float2* cand_val;
+  uint32_t cand_cap;
+  Ctl* ctl;
+  float* partial;           // COL_RESID / COL_NORM: one float per CTA
+  const float2* tw;         // twiddle table (global)
+  const uint32_t* gate;     // if non-null, the pass runs only when *gate == gate_val
+  uint32_t gate_val;
+  int nr;                   // row length N_r
+  float scale;              // 1/N_a for inverse transforms
+};
+
+struct RowArgs {
+  float2* data;             // in place, [n_rows][N_r]
+  const RowCoef* coef;      // one per row
+  const float2* tw;
+  const uint32_t* gate;     // if non-null, the pass runs only when *gate == gate_val
+  uint32_t gate_val;
+  int n_rows;
+  float scale;              // 1/N_r of the range IFFT
+};
+
+// Column tile width (columns per CTA) for a column length N: tile of 16K elements.
+__host__ __device__ constexpr int col_w(int n) { return n >= 16384 ? 1 : (16384 / n > 16 ? 16 : 16384 / n); }
+__host__ __device__ constexpr int col_threads(int n) { return n * col_w(n) / regs_for(n); }
+__host__ __device__ constexpr int row_w(int n) { return n >= 8192 ? 1 : 8192 / n; }
+__host__ __device__ constexpr int row_threads(int n) { return n * row_w(n) / regs_for(n); }
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_col(int na, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
+cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
+cudaError_t col_set_attributes(int na);
+cudaError_t launch_mask_transpose(int na, int nr, const uint32_t* mask, uint32_t* mask_t,
+                                  cudaStream_t s);
+cudaError_t row_set_attributes(int nr);
+
+struct SelArgs {
+  Ctl* ctl;
+  const uint32_t* hist;       // column-pass histogram (zeroed by sel_finish)
+  uint32_t* hist_mut;
+  uint32_t* hist2;            // radix-select histogram [4096]
+  const uint32_t* xs_idx;     // current iterate
+  const float2* xs_val;
+  const float2* xs_dx;
+  const uint32_t* cand_idx;
+  const float2* cand_val;
+  uint32_t cand_cap;
+  uint32_t* tile_cnt;         // [n_tiles]
+  uint32_t* tile_cur;         // [n_tiles]
+  uint32_t* xo_off;           // next iterate (bucketed)
+  uint32_t* xo_idx;
+  float2* xo_val;
+  const float* partial;       // residual partials of the column pass (COL_RESID)
+  const float* partial_norm;  // NIHT denominator partials (COL_NORM)
+  int n_partial;
+  IterStat* stats;
+  int64_t K;
+  int64_t n;
+  int nr;
+  int col_tile;               // columns per column-pass tile
+  int n_tiles;
+  int thresh;                 // 0 soft, 1 half
+  int mu_mode;                // 0 fixed, 1 NIHT
+  float mu_fixed;
+};
+
+cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_sel_round(const SelArgs& a, int level, cudaStream_t s);
+cudaError_t launch_sel_pick(const SelArgs& a, int level, cudaStream_t s);
+cudaError_t launch_thr_count(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_thr_scan(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_thr_scatter(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_thr_scatter_mode(const SelArgs& a, int raw, cudaStream_t s);
+cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
+cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
+
+// list <-> dense
+cudaError_t launch_list_to_dense(const uint32_t* off, const uint32_t* idx, const float2* val,
+                                 int n_tiles, float2* dense, cudaStream_t s);
+cudaError_t launch_dense_count(const float2* dense, int na, int nr, int col_tile,
+                               uint32_t* tile_cnt, cudaStream_t s);
+cudaError_t launch_dense_scan(uint32_t* tile_cnt, uint32_t* tile_cur, uint32_t* off, int n_tiles,
+                              Ctl* ctl, cudaStream_t s);
+cudaError_t launch_dense_scatter(const float2* dense, int na, int nr, int col_tile,
+                                 uint32_t* tile_cur, uint32_t* idx, float2* val, cudaStream_t s);
+
+}  // namespace csar

@@ -1,0 +1,96 @@
+// row_pass.cu — range (row, contiguous-axis) passes with the chirp-scaling phases.
+//
+// One CTA owns row_w(N) whole rows of the range-Doppler array (azimuth-frequency
+// rows).  Per row, in registers:
+//
+//   x exp(j 2 pi phi_pro(j'))  ->  range FFT  ->  x exp(j 2 pi phi_mid(m))
+//       ->  range IFFT  ->  x exp(j 2 pi phi_epi(j')) / N_r
+//
+// With (pro, mid, epi) = (H1, H2, H3) this is the middle of the focusing operator M;
+// with the conjugates (H3*, H2*, H1*) it is the middle of G (Section III-C/D).
+// j' = j - N_r/2 is the signed range-time bin, m the signed range-frequency bin;
+// each phase is evaluated on the fly from per-row FP64-derived coefficients
+// (phase.cuh), so the pass reads and writes each element exactly once.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace csar {
+
+template <int N>
+__global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
+  constexpr int WR = row_w(N);
+  constexpr int R = regs_for(N);
+  constexpr int QR = N / R;
+  using L = Layout<N, WR, false>;
+  extern __shared__ float2 smem[];
+  if (a.gate && *a.gate != a.gate_val) return;
+  float2* sm = smem;
+  float2* tw = smem + L::kSmemElems;
+  load_twiddles(tw, a.tw);
+  const int tid = threadIdx.x;
+  const int w = tid / QR, t = tid % QR;
+  const int row = blockIdx.x * WR + w;
+  const bool live = row < a.n_rows;
+  const RowCoef* cp = a.coef + (live ? row : 0);
+  float2* rp = a.data + (size_t)(live ? row : 0) * N;
+  float2 v[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+  {
+    const PhaseCoef c = cp->pro;
+    phase_ap<R, 0, R>(v, c, t - N / 2, QR, 1.f, phase_second_diff(c, QR));
+  }
+  fft<N, false, L, false>(v, sm, tw, t, w);
+  {
+    // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
+    const PhaseCoef c = cp->mid;
+    const float2 dd = phase_second_diff(c, QR);
+    phase_ap<R, 0, R / 2>(v, c, t, QR, 1.f, dd);
+    phase_ap<R, R / 2, R>(v, c, t - (R / 2) * QR, QR, 1.f, dd);
+  }
+  fft<N, true, L, false>(v, sm, tw, t, w);
+  {
+    const PhaseCoef c = cp->epi;
+    phase_ap<R, 0, R>(v, c, t - N / 2, QR, a.scale, phase_second_diff(c, QR));
+  }
+  if (live) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
+  }
+}
+
+template <int N>
+static size_t row_smem() {
+  using L = Layout<N, row_w(N), false>;
+  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2);
+}
+
+#define CSAR_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+cudaError_t row_set_attributes(int nr) {
+  switch (nr) {
+#define CSAR_CASE(N)                                                                     \
+  case N:                                                                                \
+    return cudaFuncSetAttribute(k_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                (int)row_smem<N>());
+    CSAR_ROW_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s) {
+  switch (nr) {
+#define CSAR_CASE(N)                                                              \
+  case N: {                                                                       \
+    const int grid = (a.n_rows + row_w(N) - 1) / row_w(N);                        \
+    k_row<N><<<grid, row_threads(N), row_smem<N>(), s>>>(a);                      \
+    return cudaGetLastError();                                                    \
+  }
+    CSAR_ROW_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace csar

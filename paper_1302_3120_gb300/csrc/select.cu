@@ -1,0 +1,475 @@
+// select.cu — the threshold of Section IV-B: sigma = |b|_(K+1), the (K+1)-th largest
+// magnitude of b = X + mu Delta X, and the complex soft / half shrinkage of b.
+//
+// The column pass COL_SELECT has already (a) recorded Delta X on the support of the
+// current K-sparse iterate and (b) histogrammed |Delta X|^2 of every off-support
+// element (4096 bins on the float bit pattern) and compacted those above a cut.
+// Off-support b = mu Delta X orders like |Delta X|, so:
+//
+//   sel_check   finds the histogram bin holding the (K+1)-th largest off-support
+//               |Delta X|^2; if the cut was above that bin's lower edge (or the
+//               candidate buffer overflowed) it asks for one exact re-pass.
+//   sel_round/  three rounds of radix select (12 + 12 + 8 key bits) over the union
+//   sel_pick    {support} u {candidates} give the exact key of |b|_(K+1)^2.
+//   thr_count/  strict |b| > sigma entries are counted per column tile, scanned,
+//   thr_scan/   shrunk and scattered into the next bucketed iterate (at most K
+//   thr_scatter entries).
+//   sel_finish  statistics, next cut guess, counters reset.
+//
+// No kernel waits on another CTA: every dependency is a kernel boundary.
+#include <cfloat>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace csar {
+
+constexpr int kSelThreads = 1024;   // single-CTA kernels
+constexpr int kGridThreads = 512;   // grid-stride kernels
+
+__device__ __forceinline__ uint32_t key_of(float2 b) { return __float_as_uint(cabs2(b)) & 0x7fffffffu; }
+
+// b of union element e: on-support entries first (X + mu dX), then candidates (mu dX).
+__device__ __forceinline__ float2 union_b(const SelArgs& a, uint32_t e, uint32_t nx, float mu,
+                                          uint32_t* idx) {
+  if (e < nx) {
+    *idx = a.xs_idx[e];
+    const float2 x = a.xs_val[e];
+    const float2 d = a.xs_dx[e];
+    return make_float2(fmaf(mu, d.x, x.x), fmaf(mu, d.y, x.y));
+  }
+  const uint32_t c = e - nx;
+  *idx = a.cand_idx[c];
+  const float2 d = a.cand_val[c];
+  return make_float2(mu * d.x, mu * d.y);
+}
+
+__device__ __forceinline__ uint32_t union_size(const Ctl* c, uint32_t cap) {
+  const uint32_t nc = c->cand_count < cap ? c->cand_count : cap;
+  return c->nx + nc;
+}
+
+// Shrinkage of b at threshold sigma (|b| > sigma is guaranteed by the caller).
+//   soft (Eq. (9), complex sgn):  b (1 - sigma/|b|)
+//   half (q = 1/2, the L_1/2 thresholding of [Xu2010]) with lambda mu chosen so that
+//   the jump point equals sigma: b (2/3)(1 + cos(2pi/3 - (2/3) acos(c (3 sigma/|b|)^1.5))),
+//   c = sqrt(96)/72.
+__device__ __forceinline__ float2 shrink(float2 b, float sigma, int kind) {
+  const float m = sqrtf(cabs2(b));
+  float f;
+  if (kind == 0) {
+    f = 1.f - sigma / m;
+  } else {
+    const float u = 3.f * sigma / m;
+    const float arg = fminf(0.13608276348795434f * u * sqrtf(u), 1.f);
+    const float phi = acosf(arg);
+    f = (2.f / 3.f) * (1.f + cosf(2.0943951023931957f - (2.f / 3.f) * phi));
+  }
+  return make_float2(b.x * f, b.y * f);
+}
+
+// Whole-block search, h[0..nb) with nb a multiple of 1024 or nb <= 1024:
+// largest bin b with S(b) = sum_{i >= b} h[i] >= target; *above = S(b+1).
+// Returns -1 if S(0) < target.  Uses sh (>= 1024 u64).  All threads get the result.
+__device__ int find_bin(const uint32_t* h, int nb, uint64_t target, uint64_t* above,
+                        unsigned long long* sh) {
+  __shared__ int res_b;
+  __shared__ unsigned long long res_above;
+  const int tid = threadIdx.x;
+  const int per = nb >= kSelThreads ? nb / kSelThreads : 1;
+  const int lo = tid * per;
+  unsigned long long cs = 0;
+  if (lo < nb)
+    for (int i = 0; i < per; ++i) cs += h[lo + i];
+  sh[tid] = cs;
+  if (tid == 0) { res_b = -1; res_above = 0; }
+  __syncthreads();
+  // inclusive suffix scan over sh[0..1024)
+  for (int off = 1; off < kSelThreads; off <<= 1) {
+    const unsigned long long add = (tid + off < kSelThreads) ? sh[tid + off] : 0ull;
+    __syncthreads();
+    sh[tid] += add;
+    __syncthreads();
+  }
+  const unsigned long long suf = sh[tid];                                   // S(lo)
+  const unsigned long long nxt = tid + 1 < kSelThreads ? sh[tid + 1] : 0ull;  // S(lo+per)
+  if (lo < nb && suf >= target && nxt < target) {
+    unsigned long long acc = nxt;
+    for (int i = per - 1; i >= 0; --i) {
+      const unsigned long long s2 = acc + h[lo + i];
+      if (s2 >= target) { res_b = lo + i; res_above = acc; break; }
+      acc = s2;
+    }
+  }
+  __syncthreads();
+  *above = res_above;
+  return res_b;
+}
+
+// ------------------------------------------------------------------ check / repass
+__global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
+  __shared__ unsigned long long sh[kSelThreads];
+  Ctl* c = a.ctl;
+  const uint64_t target = (uint64_t)a.K + 1;
+  uint64_t above = 0;
+  const int b = find_bin(a.hist, kHistBins, target, &above, sh);
+  if (threadIdx.x == 0) {
+    uint32_t low = b > 0 ? ((uint32_t)b << kHistShift) : 0u;
+    if (low < kMinKey) low = kMinKey;
+    const bool ok = c->cut_key <= low && c->cand_count <= a.cand_cap;
+    c->need_repass = ok ? 0u : 1u;
+    if (!ok) {
+      c->cut_key = low;
+      c->cand_count = 0u;
+    }
+    // NIHT with an empty support (first iteration): select on Delta X (mu = 1),
+    // then the step is computed on that top-K support and applied afterwards
+    c->niht_first = (a.mu_mode == 1 && c->nx == 0u) ? 1u : 0u;
+    if (a.mu_mode == 0 || c->nx == 0u) c->mu = a.mu_mode == 0 ? a.mu_fixed : 1.f;
+  }
+  // capacity check of the re-pass: off-support keys >= the new cut
+  if (threadIdx.x == 0 && c->need_repass) {
+    const int lb = b > 0 ? b : (int)(kMinKey >> kHistShift);
+    unsigned long long cnt = 0;
+    for (int i = lb; i < (int)kHistBins; ++i) cnt += a.hist[i];
+    if (cnt > a.cand_cap) atomicOr(&c->err, kErrCapacity);
+  }
+}
+
+// ------------------------------------------------------------------ radix select
+__global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level) {
+  __shared__ uint32_t h[kHistBins];
+  const Ctl* c = a.ctl;
+  if (c->sel_prefix == 0xffffffffu) return;   // selection already decided
+  for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const uint32_t nx = c->nx;
+  const uint32_t nu = union_size(c, a.cand_cap);
+  const float mu = c->mu;
+  const uint32_t prefix = c->sel_prefix;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
+    uint32_t idx;
+    const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
+    if (key < kMinKey) continue;
+    if (level == 0) {
+      atomicAdd(&h[key >> 20], 1u);
+    } else if (level == 1) {
+      if ((key >> 20) == prefix) atomicAdd(&h[(key >> 8) & 4095u], 1u);
+    } else {
+      if ((key >> 8) == prefix) atomicAdd(&h[key & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&a.hist2[i], h[i]);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) {
+  __shared__ unsigned long long sh[kSelThreads];
+  Ctl* c = a.ctl;
+  const bool done = c->sel_prefix == 0xffffffffu && level > 0;
+  if (!done) {
+    const uint64_t target = level == 0 ? (uint64_t)a.K + 1 : (uint64_t)c->sel_rank;
+    const int nb = level == 2 ? 256 : (int)kHistBins;
+    uint64_t above = 0;
+    const int b = find_bin(a.hist2, nb, target, &above, sh);
+    if (threadIdx.x == 0) {
+      if (b < 0) {
+        // fewer than K+1 nonzero magnitudes: keep every nonzero element
+        c->sel_prefix = 0xffffffffu;
+        c->sigma2_key = 0u;
+        c->sigma = 0.f;
+      } else {
+        c->sel_rank = (uint32_t)(target - above);
+        if (level == 0) {
+          c->sel_prefix = (uint32_t)b;
+        } else if (level == 1) {
+          c->sel_prefix = (c->sel_prefix << 12) | (uint32_t)b;
+        } else {
+          const uint32_t key = (c->sel_prefix << 8) | (uint32_t)b;
+          c->sigma2_key = key;
+          c->sigma = sqrtf(__uint_as_float(key));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x) a.hist2[i] = 0u;
+}
+
+// ------------------------------------------------------------------ threshold
+__device__ __forceinline__ bool kept(uint32_t key, uint32_t s2) { return key > s2 && key >= kMinKey; }
+
+__global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
+  const Ctl* c = a.ctl;
+  const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
+  const float mu = c->mu;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
+    uint32_t idx;
+    const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
+    if (kept(key, s2)) atomicAdd(&a.tile_cnt[(idx % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+  }
+}
+
+// Exclusive scan of the per-tile counts into the next iterate's offsets.
+__global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
+  __shared__ unsigned long long sh[kSelThreads];
+  const int tid = threadIdx.x;
+  const int per = (a.n_tiles + kSelThreads - 1) / kSelThreads;
+  const int lo = tid * per;
+  unsigned long long s = 0;
+  for (int i = 0; i < per; ++i)
+    if (lo + i < a.n_tiles) s += a.tile_cnt[lo + i];
+  sh[tid] = s;
+  __syncthreads();
+  for (int off = 1; off < kSelThreads; off <<= 1) {   // inclusive prefix scan
+    const unsigned long long add = tid >= off ? sh[tid - off] : 0ull;
+    __syncthreads();
+    sh[tid] += add;
+    __syncthreads();
+  }
+  unsigned long long run = tid ? sh[tid - 1] : 0ull;
+  for (int i = 0; i < per; ++i) {
+    const int k = lo + i;
+    if (k < a.n_tiles) {
+      a.xo_off[k] = (uint32_t)run;
+      a.tile_cur[k] = (uint32_t)run;
+      run += a.tile_cnt[k];
+      a.tile_cnt[k] = 0u;
+    }
+  }
+  if (tid == kSelThreads - 1) {
+    a.xo_off[a.n_tiles] = (uint32_t)sh[kSelThreads - 1];
+    a.ctl->nnz = (uint32_t)sh[kSelThreads - 1];
+  }
+}
+
+// raw != 0: store b itself (the NIHT support list of the first iteration).
+__global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw) {
+  const Ctl* c = a.ctl;
+  raw = raw && c->niht_first;
+  const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
+  const float mu = c->mu, sigma = c->sigma;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
+    uint32_t idx;
+    const float2 b = union_b(a, e, nx, mu, &idx);
+    if (!kept(key_of(b), s2)) continue;
+    const uint32_t tile = (idx % (uint32_t)a.nr) / (uint32_t)a.col_tile;
+    const uint32_t pos = atomicAdd(&a.tile_cur[tile], 1u);
+    a.xo_idx[pos] = idx;
+    a.xo_val[pos] = raw ? b : shrink(b, sigma, a.thresh);
+  }
+}
+
+// NIHT: mu = ||Delta X_Gamma||^2 / ||S . G(Delta X_Gamma)||^2 (den from the column
+// pass partials).  first != 0: Gamma is the new list (values = Delta X, first
+// iteration); the list values are then replaced by their shrinkage at mu*sigma.
+__global__ void __launch_bounds__(kSelThreads) k_niht_mu(SelArgs a, int first) {
+  __shared__ double sd[kSelThreads];
+  __shared__ double sn[kSelThreads];
+  __shared__ float mu_s;
+  Ctl* c = a.ctl;
+  if (c->niht_first != (uint32_t)first) return;
+  const int tid = threadIdx.x;
+  double den = 0.0, num = 0.0;
+  for (int i = tid; i < a.n_partial; i += kSelThreads) den += (double)a.partial_norm[i];
+  const uint32_t n_g = first ? c->nnz : c->nx;
+  const float2* vals = first ? a.xo_val : a.xs_dx;
+  for (uint32_t e = tid; e < n_g; e += kSelThreads) num += (double)cabs2(vals[e]);
+  sd[tid] = den;
+  sn[tid] = num;
+  __syncthreads();
+  for (int off = kSelThreads / 2; off > 0; off >>= 1) {
+    if (tid < off) { sd[tid] += sd[tid + off]; sn[tid] += sn[tid + off]; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double d = sd[0], nm = sn[0];
+    const float mu = (nm > 0.0 && d > 0.0) ? (float)(nm / d) : 1.f;
+    c->niht_num = nm;
+    c->niht_den = d;
+    c->mu = mu;
+    if (first) c->sigma = c->sigma * mu;
+    mu_s = mu;
+  }
+  __syncthreads();
+  if (first) {
+    const float mu = mu_s, sigma = c->sigma;
+    for (uint32_t e = tid; e < n_g; e += kSelThreads) {
+      const float2 d = a.xo_val[e];
+      a.xo_val[e] = shrink(make_float2(mu * d.x, mu * d.y), sigma, a.thresh);
+    }
+  }
+}
+
+// Statistics, next cut guess and counter resets (after the scatter).
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
+  __shared__ double sd[kSelThreads];
+  Ctl* c = a.ctl;
+  const int tid = threadIdx.x;
+  double r = 0.0;
+  for (int i = tid; i < a.n_partial; i += kSelThreads) r += (double)a.partial[i];
+  sd[tid] = r;
+  __syncthreads();
+  for (int off = kSelThreads / 2; off > 0; off >>= 1) {
+    if (tid < off) sd[tid] += sd[tid + off];
+    __syncthreads();
+  }
+  for (int i = tid; i < (int)kHistBins; i += kSelThreads) a.hist_mut[i] = 0u;
+  if (tid == 0) {
+    IterStat st;
+    st.resid_sq = sd[0];
+    st.mu = c->mu;
+    st.sigma = c->sigma;
+    st.nnz = c->nnz;
+    st.pad = 0;
+    if (a.stats) a.stats[c->iter] = st;
+    c->iter += 1u;
+    // next cut on |Delta X|^2: half of (sigma/mu)^2, i.e. 3 dB below the current
+    // threshold (checked, and re-done exactly if wrong, by the next sel_check)
+    const float mu = c->mu > 0.f ? c->mu : 1.f;
+    const float s = c->sigma / mu;
+    float g = 0.5f * s * s;
+    uint32_t cut = __float_as_uint(g);
+    if (!(g > 0.f) || !isfinite(g)) cut = kNoCandidates;
+    if (cut < kMinKey) cut = kMinKey;
+    c->cut_key = cut;
+    c->cand_count = 0u;
+    c->nx = c->nnz;
+    c->sel_prefix = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ list <-> dense
+__global__ void k_list_to_dense(const uint32_t* off, const uint32_t* idx, const float2* val,
+                                int n_tiles, float2* dense) {
+  const uint32_t n = off[n_tiles];
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    dense[idx[e]] = val[e];
+}
+
+__global__ void k_dense_count(const float2* dense, int na, int nr, int col_tile, uint32_t* cnt) {
+  const size_t n = (size_t)na * nr;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = dense[i];
+    if (v.x != 0.f || v.y != 0.f) atomicAdd(&cnt[(i % nr) / col_tile], 1u);
+  }
+}
+
+__global__ void k_dense_scatter(const float2* dense, int na, int nr, int col_tile, uint32_t* cur,
+                                uint32_t* idx, float2* val) {
+  const size_t n = (size_t)na * nr;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = dense[i];
+    if (v.x != 0.f || v.y != 0.f) {
+      const uint32_t p = atomicAdd(&cur[(i % nr) / col_tile], 1u);
+      idx[p] = (uint32_t)i;
+      val[p] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_dense_scan(uint32_t* cnt, uint32_t* cur, uint32_t* off,
+                                                            int n_tiles, Ctl* ctl) {
+  __shared__ unsigned long long sh[kSelThreads];
+  const int tid = threadIdx.x;
+  const int per = (n_tiles + kSelThreads - 1) / kSelThreads;
+  const int lo = tid * per;
+  unsigned long long s = 0;
+  for (int i = 0; i < per; ++i)
+    if (lo + i < n_tiles) s += cnt[lo + i];
+  sh[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < kSelThreads; o <<= 1) {
+    const unsigned long long add = tid >= o ? sh[tid - o] : 0ull;
+    __syncthreads();
+    sh[tid] += add;
+    __syncthreads();
+  }
+  unsigned long long run = tid ? sh[tid - 1] : 0ull;
+  for (int i = 0; i < per; ++i) {
+    const int k = lo + i;
+    if (k < n_tiles) {
+      off[k] = (uint32_t)run;
+      cur[k] = (uint32_t)run;
+      run += cnt[k];
+      cnt[k] = 0u;
+    }
+  }
+  if (tid == kSelThreads - 1) {
+    off[n_tiles] = (uint32_t)sh[kSelThreads - 1];
+    if (ctl) ctl->nx = (uint32_t)sh[kSelThreads - 1];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static int g_grid_ctas = 0;
+static int grid_ctas() {
+  if (!g_grid_ctas) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_grid_ctas = 2 * (sms > 0 ? sms : 1);
+  }
+  return g_grid_ctas;
+}
+
+cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s) {
+  k_sel_check<<<1, kSelThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_sel_round(const SelArgs& a, int level, cudaStream_t s) {
+  k_sel_round<<<grid_ctas(), kGridThreads, 0, s>>>(a, level);
+  return cudaGetLastError();
+}
+cudaError_t launch_sel_pick(const SelArgs& a, int level, cudaStream_t s) {
+  k_sel_pick<<<1, kSelThreads, 0, s>>>(a, level);
+  return cudaGetLastError();
+}
+cudaError_t launch_thr_count(const SelArgs& a, cudaStream_t s) {
+  k_thr_count<<<grid_ctas(), kGridThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_thr_scan(const SelArgs& a, cudaStream_t s) {
+  k_thr_scan<<<1, kSelThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_thr_scatter_mode(const SelArgs& a, int raw, cudaStream_t s) {
+  k_thr_scatter<<<grid_ctas(), kGridThreads, 0, s>>>(a, raw);
+  return cudaGetLastError();
+}
+cudaError_t launch_thr_scatter(const SelArgs& a, cudaStream_t s) { return launch_thr_scatter_mode(a, 0, s); }
+cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s) {
+  k_niht_mu<<<1, kSelThreads, 0, s>>>(a, first);
+  return cudaGetLastError();
+}
+cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s) { return launch_niht_mu_mode(a, 0, s); }
+cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s) {
+  k_sel_finish<<<1, kSelThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_to_dense(const uint32_t* off, const uint32_t* idx, const float2* val,
+                                 int n_tiles, float2* dense, cudaStream_t s) {
+  k_list_to_dense<<<grid_ctas(), kGridThreads, 0, s>>>(off, idx, val, n_tiles, dense);
+  return cudaGetLastError();
+}
+cudaError_t launch_dense_count(const float2* dense, int na, int nr, int col_tile, uint32_t* cnt,
+                               cudaStream_t s) {
+  k_dense_count<<<grid_ctas() * 2, kGridThreads, 0, s>>>(dense, na, nr, col_tile, cnt);
+  return cudaGetLastError();
+}
+cudaError_t launch_dense_scan(uint32_t* cnt, uint32_t* cur, uint32_t* off, int n_tiles, Ctl* ctl,
+                              cudaStream_t s) {
+  k_dense_scan<<<1, kSelThreads, 0, s>>>(cnt, cur, off, n_tiles, ctl);
+  return cudaGetLastError();
+}
+cudaError_t launch_dense_scatter(const float2* dense, int na, int nr, int col_tile, uint32_t* cur,
+                                 uint32_t* idx, float2* val, cudaStream_t s) {
+  k_dense_scatter<<<grid_ctas() * 2, kGridThreads, 0, s>>>(dense, na, nr, col_tile, cur, idx, val);
+  return cudaGetLastError();
+}
+
+}  // namespace csar

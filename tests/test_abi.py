@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/csar.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "csar.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(csar_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
+              "csar_solve", "csar_solve_host", "csar_plan_check", "csar_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1302_3120_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+    from paper_1302_3120_gb300 import csar
+    assert csar.csar_version() >= 10000
+    for s in csar.EXPORTS:
+        assert s in declared_symbols()
+
+
+def test_invalid_arguments_rejected_on_host():
+    """Parameter validation happens before any CUDA call, so it runs without a GPU."""
+    import synth
+    from paper_1302_3120_gb300 import csar
+    bad = synth.airborne(100, 256)          # not a power of two
+    try:
+        csar.csar_plan_create(bad)
+    except csar.CsarError as e:
+        assert e.status == 1 and "power of two" in str(e)
+    else:
+        raise AssertionError("plan accepted n_az = 100")
+    neg = synth.Geometry(64, 64, -0.03, 150.0, 10e3, 200.0, 60e6, 1e-6, 72e6, 2.0)
+    try:
+        csar.csar_plan_create(neg)
+    except csar.CsarError as e:
+        assert e.status == 1 and "wavelength" in str(e)
+    else:
+        raise AssertionError("plan accepted a negative wavelength")
+    p = csar.params_of(synth.airborne(64, 64))
+    h = ctypes.c_void_p()
+    assert csar.lib.csar_plan_create(ctypes.byref(p), 7, ctypes.byref(h)) == 1
+    assert h.value is None
+    assert csar.lib.csar_plan_create(None, 0, ctypes.byref(h)) == 1

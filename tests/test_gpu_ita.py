@@ -1,0 +1,178 @@
+"""GPU parity of the ITA (Algorithm 1 / Eq. (25)) against the FP64 oracle: single
+iterations with every step/threshold mode, full solves on the 256^2 point-target
+workload and on distributed scenes, the degenerate cases, and the 8192^2 workload."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import crand, dev, dev_mask, host, lib
+from oracle import csa, echo, ita, metrics
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_iterate_matches(x_gpu, x_ref, b_ref, sigma_ref, rel=1e-4, band=1e-4):
+    """Identical support except entries with ||b| - sigma| <= band*sigma; values
+    within rel (relative L2) of the oracle."""
+    mag = np.abs(b_ref)
+    clear = np.abs(mag - sigma_ref) > band * max(sigma_ref, 1e-30)
+    sup_gpu = x_gpu != 0
+    sup_ref = x_ref != 0
+    assert np.array_equal(sup_gpu[clear], sup_ref[clear]), (
+        int(np.sum(sup_gpu[clear] != sup_ref[clear])))
+    if np.any(x_ref):
+        assert metrics.rel_l2(x_gpu, x_ref) < rel
+    else:
+        assert np.abs(x_gpu).max() < 1e-6
+
+
+def _problem(seed, na=256, nr=256, frac=0.01, rate=0.5, geom=synth.airborne, noise_db=None):
+    g = geom(na, nr)
+    rng = np.random.default_rng(seed)
+    x = synth.sparse_rayleigh(rng, na, nr, frac)
+    y = csa.observe_G(g, x)
+    if noise_db is not None:
+        y = echo.add_noise(synth.cn_noise(rng, y.shape), y, noise_db)
+    mask = synth.bernoulli_mask(rng, na, nr, rate)
+    return g, x, mask * y, mask
+
+
+@pytest.mark.parametrize("mu_mode,mu,kind,x0", [
+    ("fixed", 1.0, "soft", "sparse"), ("fixed", 0.7, "half", "sparse"),
+    ("niht", 1.0, "soft", "sparse"), ("niht", 1.0, "half", "zero"), ("fixed", 1.3, "soft", "zero"),
+])
+@pytest.mark.parametrize("shape", [(256, 256), (64, 512), (1024, 128)])
+def test_single_iteration(mu_mode, mu, kind, x0, shape):
+    csar = lib()
+    import torch
+    na, nr = shape
+    g, xt, y, mask = _problem(5, na, nr)
+    rng = np.random.default_rng(9)
+    x = (synth.sparse_rayleigh(rng, na, nr, 0.02) if x0 == "sparse"
+         else np.zeros((na, nr), complex))
+    K = int(0.01 * na * nr)
+    x_ref, st, b_ref = ita.ita_iteration(g, y, mask, x, K, mu_mode, mu, kind, return_b=True)
+    plan = csar.csar_plan_create(g)
+    X = dev(x)
+    sig = torch.zeros(1, dtype=torch.float32, device="cuda")
+    csar.csar_ita_step(plan, dev(y), dev_mask(mask), X, K, mu_mode, mu, kind, sigma=sig)
+    torch.cuda.synchronize()
+    csar.csar_plan_check(plan)
+    assert abs(sig.item() - st.sigma) <= 1e-5 * st.sigma
+    xg = host(X)
+    assert np.count_nonzero(xg) <= K
+    assert_iterate_matches(xg, x_ref, b_ref, st.sigma)
+
+
+def test_config1_point_targets_solve():
+    """256^2 airborne, 5 unit point targets from the exact echo model + 30 dB noise,
+    50% Bernoulli sampling, K = 5, 100 iterations: the GPU recovers the 5 pixels and
+    matches the oracle image."""
+    csar = lib()
+    g = synth.airborne(256, 256)
+    rng = np.random.default_rng(0)
+    rows, cols, amps = synth.point_targets(rng, 256, 256, 5)
+    s = echo.point_echo(g, rows, cols, amps)
+    s = echo.add_noise(synth.cn_noise(rng, s.shape), s, 30.0)
+    mask = synth.bernoulli_mask(rng, 256, 256, 0.5)
+    y = mask * s
+    x_ref, st_ref = ita.ita(g, y, mask, 5, 100)
+    plan = csar.csar_plan_create(g)
+    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), 5, 100, stats=True)
+    xg = host(X)
+    assert set(zip(*np.nonzero(xg))) == set(zip(rows.tolist(), cols.tolist()))
+    assert metrics.rel_l2(xg, x_ref) < 1e-3
+    sig_ref = np.array([s_.sigma for s_ in st_ref])
+    assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-3
+    res_ref = np.array([s_.resid_sq for s_ in st_ref])
+    assert np.max(np.abs(st["resid_sq"] - res_ref) / res_ref) < 1e-3
+
+
+@pytest.mark.parametrize("mu_mode,kind", [("fixed", "soft"), ("niht", "soft"), ("fixed", "half")])
+def test_distributed_scene_solve(mu_mode, kind):
+    """512^2 airborne, 1% Rayleigh scene, G(X) echo + 20 dB noise, 50% sampling,
+    K = 1% of n, 30 iterations."""
+    csar = lib()
+    g, xt, y, mask = _problem(21, 512, 512, noise_db=20.0)
+    K = int(round(0.01 * 512 * 512))
+    x_ref, st_ref = ita.ita(g, y, mask, K, 30, mu_mode=mu_mode, kind=kind)
+    plan = csar.csar_plan_create(g)
+    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 30, mu_mode=mu_mode, thresh=kind,
+                            stats=True)
+    xg = host(X)
+    assert metrics.rel_l2(xg, x_ref) < 1e-3
+    assert np.all(st["nnz"] <= K)
+    if mu_mode == "niht":
+        mu_ref = np.array([s_.mu for s_ in st_ref])
+        assert np.max(np.abs(st["mu"] - mu_ref) / mu_ref) < 1e-3
+
+
+def test_degenerate_cases():
+    csar = lib()
+    import torch
+    g, xt, y, mask = _problem(4, 128, 128)
+    plan = csar.csar_plan_create(g)
+    Y, M = dev(y), dev_mask(mask)
+    # K = 0: sigma = max |b|, nothing survives
+    assert not np.any(host(csar.csar_solve(plan, Y, M, 0, 3)))
+    # K >= n: sigma = 0, soft threshold is the identity: X^(1) = mu M(S Y)
+    x1 = host(csar.csar_solve(plan, Y, M, 128 * 128, 1))
+    assert metrics.rel_l2(x1, csa.focus_M(g, y)) < 1e-5
+    # all-zero echo and mask: the iterate stays 0
+    z = torch.zeros_like(Y)
+    assert not np.any(host(csar.csar_solve(plan, z, M, 100, 3)))
+    m0 = dev_mask(np.zeros_like(mask))
+    assert not np.any(host(csar.csar_solve(plan, Y, m0, 100, 3)))
+    # full sampling, mu = 1: every iterate equals T(M(Y)) (closed form of M G = I)
+    full = np.ones_like(mask)
+    yf = crand(np.random.default_rng(2), (128, 128))
+    xr = ita.soft_threshold(csa.focus_M(g, yf), ita.kth_largest_magnitude(csa.focus_M(g, yf), 300))
+    for iters in (1, 4):
+        xg = host(csar.csar_solve(plan, dev(yf), dev_mask(full), 300, iters))
+        assert metrics.rel_l2(xg, xr) < 1e-4
+
+
+def test_nonfinite_echo_is_reported():
+    csar = lib()
+    g, xt, y, mask = _problem(6, 64, 64)
+    y = y.copy()
+    idx = np.argwhere(mask)[0]
+    y[tuple(idx)] = np.nan
+    plan = csar.csar_plan_create(g)
+    with pytest.raises(csar.CsarError) as e:
+        csar.csar_solve(plan, dev(y), dev_mask(mask), 10, 2, stats=True)
+    assert e.value.status == 6
+
+
+def test_host_buffer_entry_point():
+    csar = lib()
+    import synth as sy
+    g, xt, y, mask = _problem(8, 256, 256)
+    plan = csar.csar_plan_create(g)
+    K = 655
+    xd = host(csar.csar_solve(plan, dev(y), dev_mask(mask), K, 10))
+    xh = csar.csar_solve_host(plan, y.astype(np.complex64), sy.pack_mask(mask), K, 10)
+    assert np.array_equal(xh.reshape(256, 256), xd.astype(np.complex64))
+
+
+def test_full_size_spaceborne_iterations():
+    """8192^2 spaceborne workload (2000 3x3 targets over -25 dB clutter, 40% sampling,
+    K = 20000) in the launch configuration the benchmark times: 2 iterations against
+    the oracle."""
+    csar = lib()
+    g = synth.spaceborne(8192, 8192)
+    rng = np.random.default_rng(0)
+    x = synth.targets_over_clutter(rng, 8192, 8192)
+    mask = synth.bernoulli_mask(rng, 8192, 8192, 0.4)
+    y = csa.observe_G(g, x)
+    del x
+    y *= mask
+    K = 20000
+    x_ref = np.zeros((8192, 8192), complex)
+    for _ in range(2):
+        x_ref, st, b_ref = ita.ita_iteration(g, y, mask, x_ref, K, return_b=True)
+    plan = csar.csar_plan_create(g)
+    X, stg = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 2, stats=True)
+    xg = host(X)
+    assert abs(stg["sigma"][-1] - st.sigma) <= 1e-4 * st.sigma
+    assert_iterate_matches(xg, x_ref, b_ref, st.sigma, rel=1e-3)
