@@ -193,13 +193,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--size", type=int, default=8192,
-                    help="profiling only: square size of a smaller case of the same workload")
+                    help="profiling only: azimuth size of a smaller case of the same workload")
+    ap.add_argument("--n-rg", type=int, default=0,
+                    help="profiling only: range size of a smaller case (default: --size)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     global N_AZ, N_RG, K_SPARSITY
-    if args.size != 8192:
-        N_AZ = N_RG = args.size
-        K_SPARSITY = max(1, int(round(20000 * (args.size / 8192) ** 2)))
+    if args.size != 8192 or args.n_rg:
+        N_AZ = args.size
+        N_RG = args.n_rg or args.size
+        K_SPARSITY = max(1, int(round(20000 * N_AZ * N_RG / 8192 ** 2)))
 
     if args.impl == "reference":
         run_reference(args, world, rank)
