@@ -1,0 +1,426 @@
+// col_pass.cuh — azimuth (column, strided-axis) passes.
+//
+// A column transform of length N_a is split over a thread-block cluster of P CTAs
+// (P = 4 at N_a = 8192, 2 at 4096, else 1), each on its own SM, that together own a
+// tile of W >= 4 adjacent columns (32-byte row segments, full DRAM sectors).  With
+// N_a = P * Q, each CTA keeps Q*W <= 8192 complex64 values (64 KiB) in registers,
+// so two CTAs fit per SM and one CTA's loads overlap the other's arithmetic.
+//
+// Forward/inverse transform "BS" (blocked rows in, strided rows out):
+//   CTA c loads rows Q*n1 + n2 for its block of n2 (all n1), does the length-P DFT
+//   over n1 and the twiddle W_N^(n2 k1) in registers, and pushes output k1 into the
+//   shared memory of CTA k1 (distributed shared memory); after a cluster barrier
+//   every CTA runs the length-Q Stockham FFT (fft.cuh) and holds rows k1 + P*k2.
+// Forward transform "SB" (strided rows in, blocked rows out), used after the
+// residue so no extra exchange is needed: the local length-Q FFT first, twiddle
+// W_N^(c k2), push to the CTA owning k2, cluster barrier, length-P DFT.
+//
+// Modes (the fused work of one ITA iteration, Algorithm 1 / Eq. (25)):
+//   COL_FWD / COL_INV      plain azimuth FFT / IFFT (operators G and M)
+//   COL_SPARSE_FWD         the K-sparse iterate scattered into a zero tile, then FFT
+//   COL_RESID              IFFT -> G(X); r = S.(Y - G(X)); FFT -> input of M
+//   COL_SELECT / REPASS    IFFT -> Delta X = M(r); Delta X at the support; histogram
+//                          of |Delta X|^2 keys and compaction of the candidates for
+//                          the (K+1)-th magnitude (Section IV-B)
+//   COL_NORM               IFFT -> G(Delta X_Gamma); sum of S.|.|^2 (NIHT step)
+#pragma once
+#include <cooperative_groups.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace csar {
+
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if constexpr (NT <= 32) {
+    return v;
+  } else {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (wid == 0) {
+      s = lane < NT / 32 ? red[lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;
+  }
+}
+
+template <int N, int P_>
+struct ColCfg {
+  static constexpr int P = P_;
+  static constexpr int Q = N / P;
+  static constexpr int W = col_w(N, P);
+  static constexpr int R = col_regs(Q);
+  static constexpr int QR = Q / R;
+  static constexpr int NT = QR * W;
+  static constexpr int RP = R / P;   // n2 values per thread in the cross-CTA step
+};
+
+// Cluster barrier (all CTAs of the cluster; release/acquire on shared memory).
+template <int P>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (P > 1) cg::this_cluster().sync();
+}
+
+// Address of element index e of column w in the shared buffer of CTA `rank`.
+template <int N, int P>
+__device__ __forceinline__ float2* peer_slot(float2* sm, int rank, int w, int e) {
+  using C = ColCfg<N, P>;
+  float2* p = sm + Layout<C::Q, C::W, true>::template at<4>(w, e);
+  if constexpr (C::P > 1) return cg::this_cluster().map_shared_rank(p, rank);
+  return p;
+}
+
+// Cross-CTA step of the blocked-in transform: v holds, per i < RP, the P values
+// n1 = 0..P-1 of n2 = c*Q/P + t + QR*i; their length-P DFT (times W_N^(n2 k1)) is
+// pushed to element n2 of CTA k1.  Then the canonical input of the local FFT is read.
+template <int N, int P, bool INV>
+__device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* sm, const float2* tw,
+                                         int c, int t, int w) {
+  using C = ColCfg<N, P>;
+  if constexpr (C::P > 1) {
+#pragma unroll
+    for (int i = 0; i < C::RP; ++i) {
+      const int n2 = c * (C::Q / C::P) + t + C::QR * i;
+      float2 a[C::P];
+#pragma unroll
+      for (int n1 = 0; n1 < C::P; ++n1) a[n1] = v[i * C::P + n1];
+      Dft<C::P, INV>::run(a);
+#pragma unroll
+      for (int k1 = 0; k1 < C::P; ++k1) {
+        const float2 x = k1 ? cmul(a[k1], twiddle_tab<INV>(tw, n2 * k1 * (kTwN / N))) : a[k1];
+        *peer_slot<N, P>(sm, k1, w, n2) = x;
+      }
+    }
+    cluster_barrier<C::P>();
+#pragma unroll
+    for (int s = 0; s < C::R; ++s) v[s] = sm[Layout<C::Q, C::W, true>::template at<4>(w, t + s * C::QR)];
+  }
+}
+
+// Global row of v-slot s before the cross step (blocked input) for CTA c.
+template <int N, int P>
+__device__ __forceinline__ int bs_in_row(int c, int t, int s) {
+  using C = ColCfg<N, P>;
+  if constexpr (C::P == 1) {
+    return t + s * C::QR;
+  } else {
+    const int i = s / C::P, n1 = s % C::P;
+    return C::Q * n1 + c * (C::Q / C::P) + t + C::QR * i;
+  }
+}
+
+// Global row of canonical slot s after the local FFT (strided output) for CTA c.
+template <int N, int P>
+__device__ __forceinline__ int strided_row(int c, int t, int s) {
+  using C = ColCfg<N, P>;
+  return c + C::P * (t + s * C::QR);
+}
+
+template <int N, int P, int MODE>
+__global__ void __launch_bounds__(ColCfg<N, P>::NT, 2) k_col(ColArgs a) {
+  static_assert(ColCfg<N, P>::NT <= 1024, "block too large");
+  using C = ColCfg<N, P>;
+  constexpr int W = C::W, R = C::R, QR = C::QR, NT = C::NT, Q = C::Q;
+  using L = Layout<Q, W, true>;
+  extern __shared__ float2 smem[];
+  float2* sm = smem;
+  float2* tw = smem + L::kSmemElems;
+  float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);   // 32 floats
+  uint32_t* hist = reinterpret_cast<uint32_t*>(red + 32);      // kHistBins (SELECT)
+
+  if constexpr (MODE == COL_REPASS) {
+    if (a.ctl->need_repass == 0) return;   // uniform for the whole grid
+  }
+  if (a.gate && *a.gate != a.gate_val) return;
+  const int c = (P > 1) ? (int)(blockIdx.x % P) : 0;      // rank in the cluster
+  const int tile = blockIdx.x / P;
+  load_twiddles(tw, a.tw);
+  const int tid = threadIdx.x;
+  const int w = tid % W, t = tid / W;
+  const int col = tile * W + w;
+  const size_t nr = (size_t)a.nr;
+  float2 v[R];
+  // every CTA of the cluster is running before any remote store (no memory ordering)
+  if constexpr (P > 1) {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  }
+
+  // ------------------------------------------------------------------ input
+  if constexpr (MODE == COL_SPARSE_FWD) {
+    // zero tile; entries whose row belongs to this CTA's blocked input set
+    for (int i = tid; i < L::kSmemElems; i += NT) sm[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const uint32_t e0 = a.xs_off[tile], e1 = a.xs_off[tile + 1];
+    for (uint32_t e = e0 + tid; e < e1; e += NT) {
+      const uint32_t idx = a.xs_idx[e];
+      const int row = (int)(idx / (uint32_t)a.nr);
+      const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
+      const int n1 = row / Q, n2 = row % Q;
+      if (P == 1 || n2 / (Q / P) == c) {
+        // slot s = i*P + n1 of thread tt, with n2 = c*Q/P + tt + QR*i
+        const int loc = (P == 1) ? row : (n2 - c * (Q / P));
+        const int tt = loc % QR, i = loc / QR;
+        const int s = (P == 1) ? i : i * P + n1;
+        sm[L::template at<4>(ww, tt + QR * s)] = a.xs_val[e];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = sm[L::template at<4>(w, t + QR * s)];
+    __syncthreads();
+  } else {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P>(c, t, s) * nr + col]);
+  }
+
+  // ------------------------------------------------------------------ transforms
+  if constexpr (MODE == COL_FWD || MODE == COL_SPARSE_FWD) {
+    bs_cross<N, P, false>(v, sm, tw, c, t, w);
+    fft<Q, false, L, true, R>(v, sm, tw, t, w);
+#pragma unroll
+    for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], v[s]);
+  } else if constexpr (MODE == COL_INV) {
+    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    fft<Q, true, L, true, R>(v, sm, tw, t, w);
+#pragma unroll
+    for (int s = 0; s < R; ++s)
+      __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], cscale(v[s], a.scale));
+  } else if constexpr (MODE == COL_RESID) {
+    // F_a r = F_a(S.Y) - F_a(S.g): the transformed masked echo (a.y) is subtracted
+    // at the store, so only the mask bits stay live between the two transforms;
+    // ||r||^2 follows from Parseval, sum |F_a r|^2 / N_a.
+    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    fft<Q, true, L, true, R>(v, sm, tw, t, w);
+    {
+      // sampling bits of this thread's R rows, pre-transposed: bit s <-> strided row s
+      const uint32_t mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        v[s] = ((mbits >> s) & 1u) ? cscale(v[s], a.scale) : make_float2(0.f, 0.f);
+    }
+    fft<Q, false, L, true, R>(v, sm, tw, t, w);
+    float acc = 0.f;
+    bool bad = false;
+    if constexpr (P == 1) {
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const size_t idx = (size_t)(t + s * QR) * nr + col;
+        const float2 r = csub(__ldcs(&a.y[idx]), v[s]);
+        bad |= !(isfinite(r.x) && isfinite(r.y));
+        acc += cabs2(r);
+        __stcs(&a.out[idx], r);
+      }
+    } else {
+      cluster_barrier<P>();   // every CTA has finished with its own buffer
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const int k2 = t + s * QR;
+        const float2 x = c ? cmul(v[s], twiddle_tab<false>(tw, c * k2 * (kTwN / N))) : v[s];
+        const int dst = k2 / (Q / P), k2l = k2 % (Q / P);
+        *peer_slot<N, P>(sm, dst, w, k2l * P + c) = x;
+      }
+      cluster_barrier<P>();
+#pragma unroll
+      for (int i = 0; i < C::RP; ++i) {
+        const int k2l = t + QR * i;
+        float2 b[P];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, k2l * P + n1)];
+        Dft<P, false>::run(b);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+          const size_t idx = (size_t)(c * (Q / P) + k2l + Q * k1) * nr + col;
+          const float2 r = csub(__ldcs(&a.y[idx]), b[k1]);
+          bad |= !(isfinite(r.x) && isfinite(r.y));
+          acc += cabs2(r);
+          __stcs(&a.out[idx], r);
+        }
+      }
+    }
+    if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
+    const float tot = block_sum<NT>(acc, red);
+    if (tid == 0) a.partial[blockIdx.x] = tot * a.scale;
+  } else if constexpr (MODE == COL_NORM) {
+    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    fft<Q, true, L, true, R>(v, sm, tw, t, w);
+    const uint32_t mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
+    float acc = 0.f;
+#pragma unroll
+    for (int s = 0; s < R; ++s) acc += ((mbits >> s) & 1u) ? cabs2(cscale(v[s], a.scale)) : 0.f;
+    const float tot = block_sum<NT>(acc, red);
+    if (tid == 0) a.partial[blockIdx.x] = tot;
+  } else {  // COL_SELECT / COL_REPASS
+    constexpr bool HIST = (MODE == COL_SELECT);
+    if constexpr (HIST) {
+      for (int i = tid; i < (int)kHistBins; i += NT) hist[i] = 0u;
+    }
+    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    fft<Q, true, L, true, R>(v, sm, tw, t, w);
+    __syncthreads();
+    // local element m of this CTA is global row c + P*m
+#pragma unroll
+    for (int s = 0; s < R; ++s) sm[L::template at<4>(w, t + s * QR)] = cscale(v[s], a.scale);
+    __syncthreads();
+    // support of the current iterate: record Delta X there, exclude from candidates
+    const uint32_t e0 = a.xs_off[tile], e1 = a.xs_off[tile + 1];
+    for (uint32_t e = e0 + tid; e < e1; e += NT) {
+      const uint32_t idx = a.xs_idx[e];
+      const int row = (int)(idx / (uint32_t)a.nr);
+      if (P > 1 && row % P != c) continue;
+      const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
+      const int p = L::template at<4>(ww, row / P);
+      if constexpr (HIST) a.xs_dx[e] = sm[p];
+      sm[p] = make_float2(__int_as_float(0x7fffffff), 0.f);
+    }
+    __syncthreads();
+    const uint32_t cut = a.ctl->cut_key;
+    constexpr uint32_t full = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
+    const int lane = tid & 31;
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const int m = t + s * QR;
+      const float2 d = sm[L::template at<4>(w, m)];
+      const bool on_support = isnan(d.x);
+      const uint32_t key = __float_as_uint(cabs2(d)) & 0x7fffffffu;
+      if constexpr (HIST) {
+        if (!on_support) atomicAdd(&hist[key >> kHistShift], 1u);
+      }
+      const bool take = !on_support && key >= cut && key >= kMinKey;
+      const uint32_t bal = __ballot_sync(full, take);
+      if (bal) {
+        const int leader = __ffs(bal) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&a.ctl->cand_count, (uint32_t)__popc(bal));
+        base = __shfl_sync(full, base, leader);
+        if (take) {
+          const uint32_t pos = base + __popc(bal & ((1u << lane) - 1u));
+          if (pos < a.cand_cap) {
+            a.cand_idx[pos] = (uint32_t)((size_t)(c + P * m) * nr + col);
+            a.cand_val[pos] = d;
+          }
+        }
+      }
+    }
+    if constexpr (HIST) {
+      __syncthreads();
+      for (int i = tid; i < (int)kHistBins; i += NT) {
+        const uint32_t h = hist[i];
+        if (h) atomicAdd(&a.hist[i], h);
+      }
+    }
+  }
+  // no CTA may exit while a peer could still address its shared memory: every remote
+  // store above is followed by a cluster barrier, so none is outstanding here
+}
+
+// Sampling mask in the residual pass's register order: word ((col*P + c)*QR + t) holds
+// the bits of rows c + P*(t + s*QR), s = 0..R-1 (bit s).
+template <int N, int P>
+__global__ void k_mask_transpose(const uint32_t* __restrict__ mask, uint32_t* __restrict__ mask_t,
+                                 int nr) {
+  using C = ColCfg<N, P>;
+  const size_t total = (size_t)nr * C::P * C::QR;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(i % C::QR);
+    const int c = (int)((i / C::QR) % C::P);
+    const int col = (int)(i / ((size_t)C::QR * C::P));
+    uint32_t wbits = 0u;
+#pragma unroll
+    for (int s = 0; s < C::R; ++s) {
+      const size_t idx = (size_t)(c + C::P * (t + s * C::QR)) * nr + col;
+      wbits |= ((__ldg(&mask[idx >> 5]) >> (idx & 31)) & 1u) << s;
+    }
+    mask_t[i] = wbits;
+  }
+}
+
+template <int N, int P>
+static size_t col_smem(int mode) {
+  using C = ColCfg<N, P>;
+  using L = Layout<C::Q, C::W, true>;
+  size_t b = (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
+             32 * sizeof(float);
+  if (mode == COL_SELECT) b += kHistBins * sizeof(uint32_t);
+  return b;
+}
+
+template <int N, int P, int MODE>
+static cudaError_t col_launch_mode(const ColArgs& a, int n_tiles, cudaStream_t s) {
+  using C = ColCfg<N, P>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_tiles * C::P);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = col_smem<N, P>(MODE);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C::P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_col<N, P, MODE>, a);
+}
+
+template <int N, int P>
+static cudaError_t col_attrs() {
+  cudaError_t e = cudaSuccess;
+#define CSAR_ATTR(M)                                                                        \
+  if (e == cudaSuccess)                                                                     \
+    e = cudaFuncSetAttribute(k_col<N, P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                             (int)col_smem<N, P>(M));                                       \
+  if (e == cudaSuccess && P > 8)                                                            \
+    e = cudaFuncSetAttribute(k_col<N, P, M>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  CSAR_ATTR(COL_FWD)
+  CSAR_ATTR(COL_INV)
+  CSAR_ATTR(COL_SPARSE_FWD)
+  CSAR_ATTR(COL_RESID)
+  CSAR_ATTR(COL_SELECT)
+  CSAR_ATTR(COL_REPASS)
+  CSAR_ATTR(COL_NORM)
+#undef CSAR_ATTR
+  return e;
+}
+
+template <int N, int P>
+static cudaError_t col_launch(ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s) {
+  switch (mode) {
+    case COL_FWD: return col_launch_mode<N, P, COL_FWD>(a, n_tiles, s);
+    case COL_INV: return col_launch_mode<N, P, COL_INV>(a, n_tiles, s);
+    case COL_SPARSE_FWD: return col_launch_mode<N, P, COL_SPARSE_FWD>(a, n_tiles, s);
+    case COL_RESID: return col_launch_mode<N, P, COL_RESID>(a, n_tiles, s);
+    case COL_SELECT: return col_launch_mode<N, P, COL_SELECT>(a, n_tiles, s);
+    case COL_REPASS: return col_launch_mode<N, P, COL_REPASS>(a, n_tiles, s);
+    case COL_NORM: return col_launch_mode<N, P, COL_NORM>(a, n_tiles, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int P>
+static cudaError_t mask_transpose(int nr, const uint32_t* mask, uint32_t* mask_t, cudaStream_t s) {
+  k_mask_transpose<N, P><<<1024, 256, 0, s>>>(mask, mask_t, nr);
+  return cudaGetLastError();
+}
+
+// Entry points of one (N, P) instantiation, used by the dispatcher in col_dispatch.cu.
+#define CSAR_COL_INSTANTIATE(N, P)                                                          \
+  cudaError_t col_attrs_##N##_##P() { return col_attrs<N, P>(); }                           \
+  cudaError_t col_launch_##N##_##P(ColMode m, const ColArgs& a, int nt, cudaStream_t s) {   \
+    return col_launch<N, P>(m, a, nt, s);                                                   \
+  }                                                                                         \
+  cudaError_t col_mask_##N##_##P(int nr, const uint32_t* mk, uint32_t* mt, cudaStream_t s) { \
+    return mask_transpose<N, P>(nr, mk, mt, s);                                             \
+  }
+
+}  // namespace csar

@@ -85,6 +85,7 @@ struct Buffers {
   float* partial = nullptr;
   float* partial_norm = nullptr;
   uint32_t* mask_t = nullptr;      // sampling mask in column-pass order
+  float2* yf = nullptr;            // F_a(S . Y): azimuth-transformed masked echo
   Ctl* ctl = nullptr;
   IterStat* stats = nullptr;
   int stats_cap = 0;
@@ -115,7 +116,7 @@ struct csar_plan_s {
   int dev = 0;
   int na = 0, nr = 0;
   int64_t n = 0;
-  int col_tile = 0, n_tiles = 0;
+  int col_p = 1, col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
   float2* tw = nullptr;
@@ -212,7 +213,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_buffers(Buffers& b) {
   void* ptrs[] = {b.z, b.off[0], b.off[1], b.idx[0], b.idx[1], b.val[0], b.val[1], b.dx, b.cand_idx,
-                  b.cand_val, b.hist, b.hist2, b.tile_cnt, b.tile_cur, b.partial, b.partial_norm, b.mask_t, b.ctl,
+                  b.cand_val, b.hist, b.hist2, b.tile_cnt, b.tile_cur, b.partial, b.partial_norm, b.mask_t, b.yf, b.ctl,
                   b.stats, b.hY, b.hMask, b.hX};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -301,7 +302,7 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   s.xo_val = b.val[nxt];
   s.partial = b.partial;
   s.partial_norm = b.partial_norm;
-  s.n_partial = plan->n_tiles;
+  s.n_partial = plan->n_tiles * plan->col_p;
   s.stats = b.stats;
   s.K = o.K;
   s.n = plan->n;
@@ -337,26 +338,27 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(mark(0));
   // G(X): F_a of the sparse iterate, range pass with conj(H3), conj(H2), conj(H1)
   c.out = b.z;
-  LK(launch_col(na, COL_SPARSE_FWD, c, nt, s));
+  LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, c, nt, s));
   LK(mark(1));
   LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
   LK(mark(2));
-  // residue r = S.(Y - G(X)) and F_a r
+  // residue r = S.(Y - G(X)), produced directly as F_a r = F_a(S.Y) - F_a(S.G(X))
   c.in = b.z;
   c.out = b.z;
-  c.y = y;
+  c.y = b.yf;
+  (void)y;
   c.mask = mask;
-  LK(launch_col(na, COL_RESID, c, nt, s));
+  LK(launch_col(na, plan->col_p, COL_RESID, c, nt, s));
   LK(mark(3));
   // M(r): range pass with H1, H2, H3
   LK(launch_row(nr, row_args(plan, b.z, plan->coef_m), s));
   LK(mark(4));
   // Delta X = F_a^-1: support values, histogram, candidates
-  LK(launch_col(na, COL_SELECT, c, nt, s));
+  LK(launch_col(na, plan->col_p, COL_SELECT, c, nt, s));
   LK(mark(5));
   SelArgs sa = sel_args(plan, cur, o);
   LK(launch_sel_check(sa, s));
-  LK(launch_col(na, COL_REPASS, c, nt, s));
+  LK(launch_col(na, plan->col_p, COL_REPASS, c, nt, s));
   if (o.mu_mode == CSAR_MU_NIHT) {
     // NIHT step on Gamma = supp X^(i) (skipped on the device when the support is empty)
     ColArgs g = col_args(plan);
@@ -366,7 +368,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[cur];
     g.xs_val = b.dx;
     g.out = b.z;
-    LK(launch_col(na, COL_SPARSE_FWD, g, nt, s));
+    LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 0u;
@@ -374,7 +376,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
-    LK(launch_col(na, COL_NORM, g, nt, s));
+    LK(launch_col(na, plan->col_p, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 0, s));
   }
   for (int lev = 0; lev < 3; ++lev) {
@@ -393,7 +395,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[nxt];
     g.xs_val = b.val[nxt];
     g.out = b.z;
-    LK(launch_col(na, COL_SPARSE_FWD, g, nt, s));
+    LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 1u;
@@ -401,7 +403,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
-    LK(launch_col(na, COL_NORM, g, nt, s));
+    LK(launch_col(na, plan->col_p, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 1, s));
   }
   LK(launch_sel_finish(sa, s));
@@ -443,12 +445,24 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
   ColArgs c = col_args(plan);
   c.in = (const float2*)in;
   c.out = (float2*)out;
-  cudaError_t e = launch_col(plan->na, COL_FWD, c, plan->n_tiles, s);
+  cudaError_t e = launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s);
   if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), s);
   c.in = (const float2*)out;
-  if (e == cudaSuccess) e = launch_col(plan->na, COL_INV, c, plan->n_tiles, s);
+  if (e == cudaSuccess) e = launch_col(plan->na, plan->col_p, COL_INV, c, plan->n_tiles, s);
   if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G" : "csar_M");
   return CSAR_OK;
+}
+
+// Per-solve preparation of the inputs: the sampling mask in column-pass order and
+// F_a(S . Y) (uses the pass-to-pass buffer as scratch).
+cudaError_t prepare_inputs(csar_plan plan, const float2* y, const uint32_t* mask, cudaStream_t s) {
+  Buffers& b = plan->b;
+  LK(launch_mask_transpose(plan->na, plan->col_p, plan->nr, mask, b.mask_t, s));
+  LK(launch_mask_apply(y, mask, b.z, plan->n, s));
+  ColArgs c = col_args(plan);
+  c.in = b.z;
+  c.out = b.yf;
+  return launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s);
 }
 
 csar_status latched(csar_plan plan) {
@@ -515,7 +529,7 @@ csar_status solve_impl(csar_plan plan, const void* Y, const uint32_t* mask, void
   if (!Y || !mask || !X) return fail(CSAR_E_INVALID, "null data pointer");
   if (csar_status st = ensure_capacity(plan, o->K, o->iters)) return st;
   Buffers& b = plan->b;
-  CK(launch_mask_transpose(plan->na, plan->nr, mask, b.mask_t, s));
+  CK(prepare_inputs(plan, (const float2*)Y, mask, s));
   // X^(0) = 0: empty list 0, fresh control block
   CK(cudaMemsetAsync(b.off[0], 0, (plan->n_tiles + 1) * sizeof(uint32_t), s));
   k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 0u, b.off[0], plan->n_tiles);
@@ -563,7 +577,8 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->na = params->n_az;
   plan->nr = params->n_rg;
   plan->n = (int64_t)plan->na * plan->nr;
-  plan->col_tile = col_w(plan->na);
+  plan->col_p = col_cluster_default(plan->na);
+  plan->col_tile = col_w(plan->na, plan->col_p);
   plan->n_tiles = plan->nr / plan->col_tile;
   const char* ng = std::getenv("CSAR_NO_GRAPH");
   plan->use_graphs = !(ng && ng[0] == '1');
@@ -577,7 +592,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
     csar_status st_ = cuda_fail(e, #call);            \
     return bail(st_);                                 \
   }
-  PK(col_set_attributes(plan->na));
+  PK(col_set_attributes(plan->na, plan->col_p));
   PK(row_set_attributes(plan->nr));
   PK(dalloc(&plan->coef_g, plan->na));
   PK(dalloc(&plan->coef_m, plan->na));
@@ -608,13 +623,14 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
     PK(cudaMemset(b.off[i], 0, (nt + 1) * sizeof(uint32_t)));
   }
   PK(dalloc(&b.dx, n));
+  PK(dalloc(&b.yf, n));
   PK(dalloc(&b.hist, kHistBins));
   PK(dalloc(&b.hist2, kHistBins));
   PK(dalloc(&b.tile_cnt, nt));
   PK(dalloc(&b.tile_cur, nt));
-  PK(dalloc(&b.partial, nt));
-  PK(dalloc(&b.partial_norm, nt));
-  PK(dalloc(&b.mask_t, (size_t)plan->nr * (plan->na / regs_for(plan->na))));
+  PK(dalloc(&b.partial, (size_t)nt * plan->col_p));
+  PK(dalloc(&b.partial_norm, (size_t)nt * plan->col_p));
+  PK(dalloc(&b.mask_t, (size_t)col_mask_words(plan->na, plan->nr, plan->col_p)));
   PK(dalloc(&b.ctl, 1));
   PK(cudaMemset(b.hist, 0, kHistBins * sizeof(uint32_t)));
   PK(cudaMemset(b.hist2, 0, kHistBins * sizeof(uint32_t)));
@@ -664,7 +680,7 @@ csar_status csar_ita_step(csar_plan plan, const void* Y_dev, const uint32_t* mas
   CK(launch_dense_scatter(X, plan->na, plan->nr, plan->col_tile, b.tile_cur, b.idx[0], b.val[0], s));
   k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 1u, b.off[0], plan->n_tiles);
   CK(cudaGetLastError());
-  CK(launch_mask_transpose(plan->na, plan->nr, mask_dev, b.mask_t, s));
+  CK(prepare_inputs(plan, (const float2*)Y_dev, mask_dev, s));
   cudaError_t e = enqueue_iteration(plan, (const float2*)Y_dev, 0, *opts, s, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "csar_ita_step");
   CK(cudaMemsetAsync(X_dev, 0, (size_t)plan->n * sizeof(float2), s));
@@ -722,7 +738,7 @@ csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t
   const int iters = opts->iters;
   std::vector<cudaEvent_t> ev((size_t)(kPasses + 1) * std::max(iters, 1));
   for (auto& x : ev) CK(cudaEventCreate(&x));
-  CK(launch_mask_transpose(plan->na, plan->nr, mask_dev, b.mask_t, s));
+  CK(prepare_inputs(plan, (const float2*)Y_dev, mask_dev, s));
   CK(cudaMemsetAsync(b.off[0], 0, (plan->n_tiles + 1) * sizeof(uint32_t), s));
   k_ctl_init<<<1, 1, 0, s>>>(b.ctl, 0u, b.off[0], plan->n_tiles);
   int cur = 0;

@@ -31,6 +31,8 @@ constexpr int kTwLo = 128;
 constexpr int kTwHi = kTwN / kTwLo;
 
 __host__ __device__ constexpr int regs_for(int q) { return q >= 32 ? 32 : 16; }
+// values per thread in the column passes (more warps per SM to hide shared-memory latency)
+__host__ __device__ constexpr int col_regs(int q) { return 16; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -260,10 +262,9 @@ struct Stages {
 
 // Full transform, canonical order in and out.  Contains __syncthreads() when Q > R:
 // every thread of the block must call it.
-template <int Q, bool INV, class L, bool COL>
-__device__ __forceinline__ void fft(float2 (&v)[regs_for(Q)], float2* sm, const float2* tw, int t,
-                                    int w) {
-  Stages<Q, regs_for(Q), INV, L, COL, 1, 4>::run(v, sm, tw, t, w);
+template <int Q, bool INV, class L, bool COL, int R = regs_for(Q)>
+__device__ __forceinline__ void fft(float2 (&v)[R], float2* sm, const float2* tw, int t, int w) {
+  Stages<Q, R, INV, L, COL, 1, 4>::run(v, sm, tw, t, w);
 }
 
 }  // namespace csar

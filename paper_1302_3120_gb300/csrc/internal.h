@@ -23,7 +23,7 @@ enum ColMode : int {
   COL_FWD = 0,        // out = F_a in
   COL_INV = 1,        // out = F_a^-1 in
   COL_SPARSE_FWD = 2, // out = F_a (list scattered into a zero tile)
-  COL_RESID = 3,      // g = F_a^-1 in; r = S.(Y - g); out = F_a r; partial ||r||^2
+  COL_RESID = 3,      // g = F_a^-1 in; out = F_a(S.Y) - F_a(S.g) = F_a r; partial ||r||^2
   COL_SELECT = 4,     // dx = F_a^-1 in; Delta X at the support; histogram; candidates
   COL_REPASS = 5,     // COL_SELECT again with the exact cut, only if ctl->need_repass
   COL_NORM = 6,       // g = F_a^-1 in; partial sum of S.|g|^2 (no store)
@@ -61,7 +61,7 @@ struct IterStat {
 struct ColArgs {
   const float2* in;
   float2* out;
-  const float2* y;          // COL_RESID: echo
+  const float2* y;          // COL_RESID: F_a(S.Y), the azimuth-transformed masked echo
   const uint32_t* mask;     // COL_RESID / COL_NORM: sampling mask in column-pass order
                             // (launch_mask_transpose)
   const uint32_t* xs_off;   // sparse iterate bucketed by column tile: offsets [tiles+1]
@@ -91,17 +91,31 @@ struct RowArgs {
   float scale;              // 1/N_r of the range IFFT
 };
 
-// Column tile width (columns per CTA) for a column length N: tile of 16K elements.
-__host__ __device__ constexpr int col_w(int n) { return n >= 16384 ? 1 : (16384 / n > 16 ? 16 : 16384 / n); }
-__host__ __device__ constexpr int col_threads(int n) { return n * col_w(n) / regs_for(n); }
+// Column passes: a cluster of P CTAs owns col_w(N, P) adjacent columns; each CTA
+// holds N*W/P <= 8192 complex64 values (64 KiB).  P is a plan choice among
+// col_cluster_ok(N, P) (see col_dispatch.cu).
+__host__ __device__ constexpr int col_w(int n, int p) {
+  return (8192 / n) * p > 16 ? 16 : (8192 / n) * p;
+}
+__host__ __device__ constexpr int col_threads(int n, int p) {
+  return (n / p) / col_regs(n / p) * col_w(n, p);
+}
+// Words of the column-order sampling mask (one per thread and column of a pass).
+__host__ __device__ constexpr long long col_mask_words(int na, int nr, int p) {
+  return (long long)nr * (na / col_regs(na / p));
+}
 __host__ __device__ constexpr int row_w(int n) { return n >= 8192 ? 1 : 8192 / n; }
 __host__ __device__ constexpr int row_threads(int n) { return n * row_w(n) / regs_for(n); }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_col(int na, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
+bool col_cluster_ok(int na, int p);
+int col_cluster_default(int na);
+cudaError_t launch_col(int na, int p, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
-cudaError_t col_set_attributes(int na);
-cudaError_t launch_mask_transpose(int na, int nr, const uint32_t* mask, uint32_t* mask_t,
+cudaError_t launch_mask_apply(const float2* y, const uint32_t* mask_bits, float2* out, long long n,
+                              cudaStream_t s);
+cudaError_t col_set_attributes(int na, int p);
+cudaError_t launch_mask_transpose(int na, int p, int nr, const uint32_t* mask, uint32_t* mask_t,
                                   cudaStream_t s);
 cudaError_t row_set_attributes(int nr);
 

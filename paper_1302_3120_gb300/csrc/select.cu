@@ -340,6 +340,17 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ masked echo
+// out = S . Y (row-major bit mask)
+__global__ void k_mask_apply(const float2* __restrict__ y, const uint32_t* __restrict__ bits,
+                             float2* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool on = (__ldg(&bits[i >> 5]) >> (i & 31)) & 1u;
+    out[i] = on ? y[i] : make_float2(0.f, 0.f);
+  }
+}
+
 // ------------------------------------------------------------------ list <-> dense
 __global__ void k_list_to_dense(const uint32_t* off, const uint32_t* idx, const float2* val,
                                 int n_tiles, float2* dense) {
@@ -448,6 +459,12 @@ cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s) {
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s) { return launch_niht_mu_mode(a, 0, s); }
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s) {
   k_sel_finish<<<1, kSelThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_apply(const float2* y, const uint32_t* mask_bits, float2* out, long long n,
+                              cudaStream_t s) {
+  k_mask_apply<<<grid_ctas() * 4, kGridThreads, 0, s>>>(y, mask_bits, out, n);
   return cudaGetLastError();
 }
 
