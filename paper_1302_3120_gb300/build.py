@@ -18,6 +18,7 @@ OUT = os.path.join(HERE, "libcsar.so")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+FLAGS += os.environ.get("CSAR_NVCC_EXTRA", "").split()
 
 
 def nvcc() -> str:

@@ -26,6 +26,7 @@
 #pragma once
 #include <cooperative_groups.h>
 
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -87,6 +88,7 @@ template <int N, int P, bool INV>
 __device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* sm, const float2* tw,
                                          int c, int t, int w) {
   using C = ColCfg<N, P>;
+  using L = Layout<C::Q, C::W, true>;
   if constexpr (C::P > 1) {
 #pragma unroll
     for (int i = 0; i < C::RP; ++i) {
@@ -103,7 +105,7 @@ __device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* s
     }
     cluster_barrier<C::P>();
 #pragma unroll
-    for (int s = 0; s < C::R; ++s) v[s] = sm[Layout<C::Q, C::W, true>::template at<4>(w, t + s * C::QR)];
+    for (int s = 0; s < C::R; ++s) v[s] = sm[L::template at<4>(w, t + s * C::QR)];
   }
 }
 
@@ -127,7 +129,7 @@ __device__ __forceinline__ int strided_row(int c, int t, int s) {
 }
 
 template <int N, int P, int MODE>
-__global__ void __launch_bounds__(ColCfg<N, P>::NT, 2) k_col(ColArgs a) {
+__global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs a) {
   static_assert(ColCfg<N, P>::NT <= 1024, "block too large");
   using C = ColCfg<N, P>;
   constexpr int W = C::W, R = C::R, QR = C::QR, NT = C::NT, Q = C::Q;
@@ -157,6 +159,14 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, 2) k_col(ColArgs a) {
 
   // ------------------------------------------------------------------ input
   if constexpr (MODE == COL_SPARSE_FWD) {
+    {
+      // groups of kDirectCols columns with few entries are transformed by k_sparse_dft
+      const int bpg = kDirectCols / W > 0 ? kDirectCols / W : 1;
+      const int grp = (tile * W) / kDirectCols;
+      const uint32_t ge = a.xs_off[(grp + 1) * bpg < a.nr / W ? (grp + 1) * bpg : a.nr / W] -
+                          a.xs_off[grp * bpg];
+      if (N >= kDirectRows && ge <= (uint32_t)kDirectMaxEntries) return;   // uniform per cluster
+    }
     // zero tile; entries whose row belongs to this CTA's blocked input set
     for (int i = tid; i < L::kSmemElems; i += NT) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();

@@ -338,6 +338,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(mark(0));
   // G(X): F_a of the sparse iterate, range pass with conj(H3), conj(H2), conj(H1)
   c.out = b.z;
+  LK(launch_sparse_dft(na, c, plan->col_tile, s));
   LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, c, nt, s));
   LK(mark(1));
   LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
@@ -368,6 +369,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[cur];
     g.xs_val = b.dx;
     g.out = b.z;
+    LK(launch_sparse_dft(na, g, plan->col_tile, s));
     LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
@@ -395,6 +397,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[nxt];
     g.xs_val = b.val[nxt];
     g.out = b.z;
+    LK(launch_sparse_dft(na, g, plan->col_tile, s));
     LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;

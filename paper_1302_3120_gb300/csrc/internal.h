@@ -94,8 +94,10 @@ struct RowArgs {
 // Column passes: a cluster of P CTAs owns col_w(N, P) adjacent columns; each CTA
 // holds N*W/P <= 8192 complex64 values (64 KiB).  P is a plan choice among
 // col_cluster_ok(N, P) (see col_dispatch.cu).
+constexpr int kColCtaElems = 8192;   // complex64 values per column-pass CTA (64 KiB)
+constexpr int kColCtasPerSm = 2;
 __host__ __device__ constexpr int col_w(int n, int p) {
-  return (8192 / n) * p > 16 ? 16 : (8192 / n) * p;
+  return (kColCtaElems / n) * p > 16 ? 16 : ((kColCtaElems / n) * p < 1 ? 1 : (kColCtaElems / n) * p);
 }
 __host__ __device__ constexpr int col_threads(int n, int p) {
   return (n / p) / col_regs(n / p) * col_w(n, p);
@@ -107,11 +109,18 @@ __host__ __device__ constexpr long long col_mask_words(int na, int nr, int p) {
 __host__ __device__ constexpr int row_w(int n) { return n >= 8192 ? 1 : 8192 / n; }
 __host__ __device__ constexpr int row_threads(int n) { return n * row_w(n) / regs_for(n); }
 
+// Direct DFT of the K-sparse iterate (k_sparse_dft): groups of kDirectCols columns
+// holding at most kDirectMaxEntries entries skip the FFT.
+constexpr int kDirectCols = 16;
+constexpr int kDirectMaxEntries = 128;
+constexpr int kDirectRows = 256;   // smallest N_a the direct DFT handles
+
 // ---------------------------------------------------------------- launchers
 bool col_cluster_ok(int na, int p);
 int col_cluster_default(int na);
 cudaError_t launch_col(int na, int p, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);
 cudaError_t launch_mask_apply(const float2* y, const uint32_t* mask_bits, float2* out, long long n,
                               cudaStream_t s);
 cudaError_t col_set_attributes(int na, int p);
