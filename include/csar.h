@@ -155,6 +155,37 @@ csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t
                                void* X_dev, const csar_opts* opts, float* pass_ms,
                                int32_t n_pass, void* stream);
 
+/* ---- Differentiable autofocus (per-pulse azimuth phase error theta) ----------------
+ * Observation A_theta X = S . (exp(j theta_eta) . G(X)) with one real phase theta_eta
+ * per echo row (pulse).  Its ITA is Algorithm 1 on the de-rotated echo
+ * exp(-j theta_eta) . Y.  Gradients follow dL = Re<grad, dz> for complex z (the
+ * torch convention).  The paper does not differentiate the method: these entry points
+ * add autofocus on top of it.  theta_dev: n_az floats (radians) on the device. */
+
+/* X^(I) of the theta-observation ITA (csar_solve on exp(-j theta).Y).  With
+ * checkpoint != 0 every iterate X^(i+1) (at most K entries), sigma_i and the
+ * (K+1)-th element are kept in the plan for csar_af_backward (soft threshold and
+ * fixed step only, else CSAR_E_UNSUPPORTED); memory: iters * K * 12 bytes. */
+csar_status csar_af_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                          const float* theta_dev, void* X_dev, const csar_opts* opts,
+                          int32_t checkpoint, void* stream);
+
+/* L = ||S . (exp(-j theta).Y - G(X))||^2 into *loss_dev (one double), and optionally
+ * grad_X = -2 M(r) (n complex64) and dL/dtheta_eta = 2 sum_tau Im(conj(r) exp(-j theta) Y)
+ * (n_az floats), r = S . (exp(-j theta).Y - G(X)).  X_dev: dense n complex64. */
+csar_status csar_af_loss(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                         const float* theta_dev, const void* X_dev, double* loss_dev,
+                         void* grad_X_dev, float* grad_theta_dev, void* stream);
+
+/* Backward through the checkpointed unroll of the last csar_af_solve on this plan:
+ * given Xbar_dev, the adjoint of X^(I) (n complex64), ADDS the theta adjoint into
+ * theta_bar_dev (n_az floats) and writes the adjoint of X^(0) into X0bar_dev (n
+ * complex64; NULL to skip).  Per iteration: the soft-threshold VJP (with the
+ * dependence of sigma = |b|_(K+1) on b), G and M of the adjoint, and a row reduction. */
+csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev,
+                             const float* theta_dev, const void* Xbar_dev,
+                             float* theta_bar_dev, void* X0bar_dev, void* stream);
+
 /* Synchronise the plan's device and report (and clear) any latched device-side
  * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, ...). */
 csar_status csar_plan_check(csar_plan plan);

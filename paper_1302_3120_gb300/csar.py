@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
-           "csar_last_error", "csar_version")
+           "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward")
 
 
 def _load() -> ctypes.CDLL:
@@ -72,10 +72,14 @@ def _load() -> ctypes.CDLL:
     lib.csar_solve_profile.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Opts),
                                        ctypes.POINTER(ctypes.c_float), i32, vp]
     lib.csar_plan_check.argtypes = [vp]
+    lib.csar_af_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(Opts), i32, vp]
+    lib.csar_af_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.csar_af_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
-                 "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check"):
+                 "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
+                 "csar_af_solve", "csar_af_loss", "csar_af_backward"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -264,3 +268,89 @@ def pack_mask_torch(mask_bool):
     words = (flat * weights).sum(dim=1)
     words = torch.where(words >= 2 ** 31, words - 2 ** 32, words)
     return words.to(torch.int32)
+
+
+# ----------------------------------------------------------------------------- autofocus
+
+def csar_af_solve(plan: Plan, Y, mask_bits, theta, K: int, iters: int, mu: float = 1.0,
+                  checkpoint: bool = True, X=None, stream=None):
+    """X^(I) of the ITA for the observation S . (exp(j theta) G X) (soft threshold,
+    fixed step); keeps per-iteration checkpoints in the plan for csar_af_backward."""
+    import torch
+    _need(Y, torch.complex64, plan.n, "Y")
+    _need(mask_bits, torch.int32, plan.n // 32, "mask_bits")
+    _need(theta, torch.float32, plan.n_az, "theta")
+    X = torch.empty_like(Y) if X is None else X
+    o = _opts(K, iters, "fixed", mu, "soft")
+    _check(lib.csar_af_solve(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(theta), _ptr(X),
+                             ctypes.byref(o), int(bool(checkpoint)), _stream(stream)), "csar_af_solve")
+    return X
+
+
+def csar_af_loss(plan: Plan, Y, mask_bits, theta, X, grads: bool = True, stream=None):
+    """(loss, grad_X, grad_theta) of ||S.(exp(-j theta) Y - G X)||^2 (device tensors)."""
+    import torch
+    _need(X, torch.complex64, plan.n, "X")
+    loss = torch.zeros(1, dtype=torch.float64, device=X.device)
+    gx = torch.empty_like(X) if grads else None
+    gt = torch.empty(plan.n_az, dtype=torch.float32, device=X.device) if grads else None
+    _check(lib.csar_af_loss(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(theta), _ptr(X), _ptr(loss),
+                            _ptr(gx) if grads else None, _ptr(gt) if grads else None,
+                            _stream(stream)), "csar_af_loss")
+    return loss, gx, gt
+
+
+def csar_af_backward(plan: Plan, Y, mask_bits, theta, Xbar, theta_bar=None, X0bar=None, stream=None):
+    """Adjoint of the last checkpointed csar_af_solve: adds into theta_bar (returned)."""
+    import torch
+    _need(Xbar, torch.complex64, plan.n, "Xbar")
+    theta_bar = (torch.zeros(plan.n_az, dtype=torch.float32, device=Xbar.device)
+                 if theta_bar is None else theta_bar)
+    _check(lib.csar_af_backward(plan.handle, _ptr(Y), _ptr(mask_bits), _ptr(theta), _ptr(Xbar),
+                                _ptr(theta_bar), _ptr(X0bar) if X0bar is not None else None,
+                                _stream(stream)), "csar_af_backward")
+    return theta_bar
+
+
+def _autograd():
+    import torch
+
+    class ITAUnroll(torch.autograd.Function):
+        """X^(I)(theta) of the unrolled ITA; backward through the checkpoints."""
+
+        @staticmethod
+        def forward(ctx, theta, plan, Y, mask_bits, K, iters, mu):
+            X = csar_af_solve(plan, Y, mask_bits, theta.detach(), K, iters, mu, checkpoint=True)
+            ctx.plan, ctx.Y, ctx.mask = plan, Y, mask_bits
+            ctx.save_for_backward(theta)
+            return X
+
+        @staticmethod
+        def backward(ctx, gX):
+            (theta,) = ctx.saved_tensors
+            tb = csar_af_backward(ctx.plan, ctx.Y, ctx.mask, theta.detach(), gX.contiguous())
+            return tb, None, None, None, None, None, None
+
+    class AutofocusLoss(torch.autograd.Function):
+        """||S.(exp(-j theta) Y - G X)||^2 with its analytic gradients."""
+
+        @staticmethod
+        def forward(ctx, X, theta, plan, Y, mask_bits):
+            loss, gx, gt = csar_af_loss(plan, Y, mask_bits, theta.detach(), X.detach())
+            ctx.save_for_backward(gx, gt)
+            return loss.reshape(())
+
+        @staticmethod
+        def backward(ctx, gl):
+            gx, gt = ctx.saved_tensors
+            return gl.to(gx.real.dtype) * gx, gl.to(gt.dtype) * gt, None, None, None
+
+    return ITAUnroll, AutofocusLoss
+
+
+def autofocus_loss(plan: Plan, Y, mask_bits, theta, K: int, iters: int, mu: float = 1.0):
+    """L(theta) = ||S.(exp(-j theta) Y - G X_I(theta))||^2 through the unrolled ITA,
+    differentiable with respect to theta (torch.autograd)."""
+    ITAUnroll, AutofocusLoss = _autograd()
+    X = ITAUnroll.apply(theta, plan, Y, mask_bits, K, iters, mu)
+    return AutofocusLoss.apply(X, theta, plan, Y, mask_bits)

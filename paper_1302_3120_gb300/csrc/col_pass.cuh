@@ -187,7 +187,10 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = sm[L::template at<4>(w, t + QR * s)];
-    __syncthreads();
+    // the buffer is reused by the cross step: peers push into it only after every CTA of
+    // the cluster has read its staged input
+    if constexpr (P > 1) cluster_barrier<P>();
+    else __syncthreads();
   } else {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P>(c, t, s) * nr + col]);

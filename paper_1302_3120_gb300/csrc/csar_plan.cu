@@ -89,6 +89,20 @@ struct Buffers {
   Ctl* ctl = nullptr;
   IterStat* stats = nullptr;
   int stats_cap = 0;
+  // autofocus
+  float2* yt = nullptr;            // exp(-j theta) . Y
+  float2* af_xbar = nullptr;
+  float2* af_bbar = nullptr;
+  float2* af_h = nullptr;
+  double* row_loss = nullptr;
+  uint32_t* ck_idx = nullptr;      // checkpoints: [iters][ck_cap]
+  float2* ck_val = nullptr;
+  CkptMeta* ck_meta = nullptr;
+  uint32_t ck_cap = 0;
+  int ck_iters_cap = 0;
+  int ck_iters = 0;                // iterations checkpointed by the last autofocus solve
+  bool ck_active = false;          // the iteration graphs copy checkpoints
+  float ck_mu = 1.f;
   // host-buffer entry point
   float2* hY = nullptr;
   uint32_t* hMask = nullptr;
@@ -103,9 +117,10 @@ struct GraphKey {
   float mu = 0.f;
   uint32_t cand_cap = 0;
   IterStat* stats = nullptr;
+  const void* ck = nullptr;
   bool operator==(const GraphKey& o) const {
     return y == o.y && mask == o.mask && K == o.K && mu_mode == o.mu_mode && thresh == o.thresh &&
-           mu == o.mu && cand_cap == o.cand_cap && stats == o.stats;
+           mu == o.mu && cand_cap == o.cand_cap && stats == o.stats && ck == o.ck;
   }
 };
 
@@ -214,7 +229,8 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_buffers(Buffers& b) {
   void* ptrs[] = {b.z, b.off[0], b.off[1], b.idx[0], b.idx[1], b.val[0], b.val[1], b.dx, b.cand_idx,
                   b.cand_val, b.hist, b.hist2, b.tile_cnt, b.tile_cur, b.partial, b.partial_norm, b.mask_t, b.yf, b.ctl,
-                  b.stats, b.hY, b.hMask, b.hX};
+                  b.stats, b.hY, b.hMask, b.hX, b.yt, b.af_xbar, b.af_bbar, b.af_h, b.row_loss,
+                  b.ck_idx, b.ck_val, b.ck_meta};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   b = Buffers();
@@ -409,6 +425,8 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     LK(launch_col(na, plan->col_p, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 1, s));
   }
+  if (b.ck_active)
+    LK(launch_ckpt_copy(b.ctl, b.idx[nxt], b.val[nxt], b.ck_idx, b.ck_val, b.ck_meta, b.ck_cap, s));
   LK(launch_sel_finish(sa, s));
   LK(mark(6));
   return cudaSuccess;
@@ -417,6 +435,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
 __global__ void k_ctl_init(Ctl* c, uint32_t nx_from_list, const uint32_t* off0, int n_tiles) {
   Ctl z{};
   z.cut_key = kNoCandidates;
+  z.jstar = 0xffffffffu;
   z.nx = nx_from_list ? off0[n_tiles] : 0u;
   *c = z;
 }
@@ -433,6 +452,17 @@ csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
     return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT or CSAR_THRESH_HALF");
   (void)plan;
   return CSAR_OK;
+}
+
+// Dense operator on device arrays: out = G(in) or M(in) (in may equal out).
+cudaError_t dense_op(csar_plan plan, const float2* in, float2* out, bool is_g, cudaStream_t s) {
+  ColArgs c = col_args(plan);
+  c.in = in;
+  c.out = out;
+  LK(launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s));
+  LK(launch_row(plan->nr, row_args(plan, out, is_g ? plan->coef_g : plan->coef_m), s));
+  c.in = out;
+  return launch_col(plan->na, plan->col_p, COL_INV, c, plan->n_tiles, s);
 }
 
 csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* stream) {
@@ -498,6 +528,7 @@ csar_status run_iterations(csar_plan plan, const float2* y, const uint32_t* mask
       k.mu = o.mu;
       k.cand_cap = plan->b.cand_cap;
       k.stats = plan->b.stats;
+      k.ck = plan->b.ck_active ? (const void*)plan->b.ck_idx : nullptr;
       if (!plan->exec[cur] || !(plan->key[cur] == k)) {
         if (plan->exec[cur]) cudaGraphExecDestroy(plan->exec[cur]);
         plan->exec[cur] = nullptr;
@@ -552,6 +583,37 @@ csar_status solve_impl(csar_plan plan, const void* Y, const uint32_t* mask, void
       if (stats->nnz) stats->nnz[i] = h[i].nnz;
     }
     return latched(plan);
+  }
+  return CSAR_OK;
+}
+
+
+csar_status ensure_af(csar_plan plan, int64_t K, int iters) {
+  Buffers& b = plan->b;
+  const size_t n = (size_t)plan->n;
+  if (!b.yt) {
+    CK(dalloc(&b.yt, n));
+    CK(dalloc(&b.af_xbar, n));
+    CK(dalloc(&b.af_bbar, n));
+    CK(dalloc(&b.af_h, n));
+    CK(dalloc(&b.row_loss, plan->na));
+  }
+  const uint32_t cap = (uint32_t)std::min<int64_t>(plan->n, std::max<int64_t>(K, 1));
+  if (iters > 0 && (b.ck_cap < cap || b.ck_iters_cap < iters)) {
+    drop_graphs(plan);
+    if (b.ck_idx) cudaFree(b.ck_idx);
+    if (b.ck_val) cudaFree(b.ck_val);
+    if (b.ck_meta) cudaFree(b.ck_meta);
+    b.ck_idx = nullptr;
+    b.ck_val = nullptr;
+    b.ck_meta = nullptr;
+    b.ck_cap = 0;
+    b.ck_iters_cap = 0;
+    CK(dalloc(&b.ck_idx, (size_t)cap * iters));
+    CK(dalloc(&b.ck_val, (size_t)cap * iters));
+    CK(dalloc(&b.ck_meta, (size_t)iters));
+    b.ck_cap = cap;
+    b.ck_iters_cap = iters;
   }
   return CSAR_OK;
 }
@@ -763,6 +825,74 @@ csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t
     }
   for (auto& x : ev) cudaEventDestroy(x);
   return latched(plan);
+}
+
+csar_status csar_af_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
+                          void* X_dev, const csar_opts* opts, int32_t checkpoint, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!theta_dev) return fail(CSAR_E_INVALID, "theta is NULL");
+  if (csar_status st = check_opts(plan, opts, true)) return st;
+  if (checkpoint && (opts->thresh != CSAR_THRESH_SOFT || opts->mu_mode != CSAR_MU_FIXED))
+    return fail(CSAR_E_UNSUPPORTED, "the autofocus backward covers soft thresholding with a fixed step");
+  if (!Y_dev || !mask_dev || !X_dev) return fail(CSAR_E_INVALID, "null data pointer");
+  DeviceGuard dg(plan->dev);
+  if (csar_status st = ensure_af(plan, opts->K, checkpoint ? opts->iters : 0)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Buffers& b = plan->b;
+  CK(launch_rotate_rows((const float2*)Y_dev, theta_dev, b.yt, plan->na, plan->nr, s));
+  b.ck_active = checkpoint != 0;
+  csar_status st = solve_impl(plan, b.yt, mask_dev, X_dev, opts, nullptr, s);
+  b.ck_active = false;
+  b.ck_iters = checkpoint ? opts->iters : 0;
+  b.ck_mu = opts->mu;
+  return st;
+}
+
+csar_status csar_af_loss(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
+                         const void* X_dev, double* loss_dev, void* grad_X_dev, float* grad_theta_dev,
+                         void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!Y_dev || !mask_dev || !theta_dev || !X_dev || !loss_dev)
+    return fail(CSAR_E_INVALID, "null data pointer");
+  DeviceGuard dg(plan->dev);
+  if (csar_status st = ensure_af(plan, 1, 0)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Buffers& b = plan->b;
+  CK(launch_rotate_rows((const float2*)Y_dev, theta_dev, b.yt, plan->na, plan->nr, s));
+  CK(dense_op(plan, (const float2*)X_dev, b.af_h, true, s));
+  CK(launch_af_resid(b.af_h, b.yt, mask_dev, plan->na, plan->nr, b.row_loss, grad_theta_dev, loss_dev, s));
+  if (grad_X_dev) {
+    CK(dense_op(plan, b.af_h, b.af_h, false, s));
+    CK(launch_scale(b.af_h, (float2*)grad_X_dev, -2.f, plan->n, s));
+  }
+  return CSAR_OK;
+}
+
+csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
+                             const void* Xbar_dev, float* theta_bar_dev, void* X0bar_dev, void* stream) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!Y_dev || !mask_dev || !theta_dev || !Xbar_dev || !theta_bar_dev)
+    return fail(CSAR_E_INVALID, "null data pointer");
+  if (plan->b.ck_iters <= 0)
+    return fail(CSAR_E_INVALID, "no checkpointed csar_af_solve on this plan");
+  DeviceGuard dg(plan->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  Buffers& b = plan->b;
+  const size_t n = (size_t)plan->n;
+  const float mu = b.ck_mu;
+  CK(launch_rotate_rows((const float2*)Y_dev, theta_dev, b.yt, plan->na, plan->nr, s));
+  CK(cudaMemcpyAsync(b.af_xbar, Xbar_dev, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  for (int i = b.ck_iters - 1; i >= 0; --i) {
+    CK(cudaMemsetAsync(b.af_bbar, 0, n * sizeof(float2), s));
+    CK(launch_af_tvjp(b.ck_idx + (size_t)i * b.ck_cap, b.ck_val + (size_t)i * b.ck_cap, b.ck_meta + i,
+                      b.af_xbar, b.af_bbar, b.ck_cap, s));
+    CK(dense_op(plan, b.af_bbar, b.af_h, true, s));                       // G(bbar)
+    CK(launch_af_mask_theta(b.af_h, b.yt, mask_dev, plan->na, plan->nr, mu, theta_bar_dev, s));
+    CK(dense_op(plan, b.af_h, b.af_h, false, s));                         // M(S.G(bbar))
+    CK(launch_af_axpy(b.af_bbar, b.af_h, mu, b.af_xbar, plan->n, s));
+  }
+  if (X0bar_dev) CK(cudaMemcpyAsync(X0bar_dev, b.af_xbar, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  return CSAR_OK;
 }
 
 }  // extern "C"

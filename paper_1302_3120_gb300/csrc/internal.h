@@ -45,8 +45,20 @@ struct Ctl {
   uint32_t niht_first;   // NIHT with an empty support: Gamma = top K of |Delta X|
   float mu;              // step of the current iteration
   float sigma;           // threshold of the current iteration
+  uint32_t jstar;        // flat index of the (K+1)-th largest |b| (0xffffffff: none)
+  uint32_t pad1;
+  float2 b_jstar;        // b at jstar
   double niht_num;       // ||Delta X_Gamma||^2
   double niht_den;       // ||S . G(Delta X_Gamma)||^2
+};
+
+// Per-iteration checkpoint of the ITA unroll (autofocus backward).
+struct CkptMeta {
+  uint32_t count;        // entries of X^(i+1)
+  float sigma;           // sigma_i
+  uint32_t jstar;        // index of the (K+1)-th largest |b| (0xffffffff: none)
+  uint32_t pad;
+  float2 b_jstar;
 };
 
 // Per-iteration statistics (device).
@@ -168,6 +180,21 @@ cudaError_t launch_thr_scatter_mode(const SelArgs& a, int raw, cudaStream_t s);
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
+
+// autofocus (autofocus.cu)
+cudaError_t launch_rotate_rows(const float2* y, const float* theta, float2* yt, int na, int nr,
+                               cudaStream_t s);
+cudaError_t launch_af_resid(float2* g, const float2* yt, const uint32_t* mask, int na, int nr,
+                            double* row_loss, float* grad_theta, double* loss, cudaStream_t s);
+cudaError_t launch_scale(const float2* in, float2* out, float alpha, long long n, cudaStream_t s);
+cudaError_t launch_af_tvjp(const uint32_t* idx, const float2* val, const CkptMeta* meta,
+                           const float2* xbar, float2* bbar, uint32_t cap, cudaStream_t s);
+cudaError_t launch_af_mask_theta(float2* g, const float2* yt, const uint32_t* mask, int na, int nr,
+                                 float mu, float* theta_bar, cudaStream_t s);
+cudaError_t launch_af_axpy(const float2* bbar, const float2* h, float mu, float2* xbar, long long n,
+                           cudaStream_t s);
+cudaError_t launch_ckpt_copy(const Ctl* ctl, const uint32_t* idx, const float2* val, uint32_t* ck_idx,
+                             float2* ck_val, CkptMeta* ck_meta, uint32_t cap, cudaStream_t s);
 
 // list <-> dense
 cudaError_t launch_list_to_dense(const uint32_t* off, const uint32_t* idx, const float2* val,

@@ -201,13 +201,14 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) 
 __device__ __forceinline__ bool kept(uint32_t key, uint32_t s2) { return key > s2 && key >= kMinKey; }
 
 __global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
-  const Ctl* c = a.ctl;
+  Ctl* c = a.ctl;
   const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
   const float mu = c->mu;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
     uint32_t idx;
     const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
     if (kept(key, s2)) atomicAdd(&a.tile_cnt[(idx % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+    else if (key == s2 && s2 >= kMinKey) atomicMin(&c->jstar, idx);   // the (K+1)-th element
   }
 }
 
@@ -246,13 +247,15 @@ __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
 
 // raw != 0: store b itself (the NIHT support list of the first iteration).
 __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw) {
-  const Ctl* c = a.ctl;
+  Ctl* c = a.ctl;
   raw = raw && c->niht_first;
   const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
   const float mu = c->mu, sigma = c->sigma;
+  const uint32_t jstar = c->jstar;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
     uint32_t idx;
     const float2 b = union_b(a, e, nx, mu, &idx);
+    if (idx == jstar) c->b_jstar = b;
     if (!kept(key_of(b), s2)) continue;
     const uint32_t tile = (idx % (uint32_t)a.nr) / (uint32_t)a.col_tile;
     const uint32_t pos = atomicAdd(&a.tile_cur[tile], 1u);
@@ -337,6 +340,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
     c->cand_count = 0u;
     c->nx = c->nnz;
     c->sel_prefix = 0u;
+    c->jstar = 0xffffffffu;
   }
 }
 
