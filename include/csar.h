@@ -186,6 +186,22 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
                              const float* theta_dev, const void* Xbar_dev,
                              float* theta_bar_dev, void* X0bar_dev, void* stream);
 
+/* y_dev = G(x_dev) without any device allocation, for callers that cannot call
+ * cudaMalloc (their allocator is owned by a host framework, they run inside stream
+ * capture, or they must not allocate after start-up).  The paper has no counterpart:
+ * it is a deployment variant of csar_G.  Same operator, layout and aliasing rules as
+ * csar_G, but no plan: the phase coefficients and FFT twiddles that a plan would keep
+ * in allocated memory go into one static device array of the library (about 580 KiB
+ * on every GPU that loads it, kept until process exit), sized for n_az <= 8192.
+ * The first call on a device looks up that array's device address (make that first
+ * call before any stream capture).  Every call rewrites the whole table, so nothing
+ * needs clearing, but calls that overlap on the GPU (other streams, other threads)
+ * share the array and race: serialise them.  Host-side calls are serialised
+ * internally.  Enqueues on `stream` (a pageable host-to-device copy of the tables,
+ * then the three passes). */
+csar_status csar_G_noalloc(const csar_params* params, const void* x_dev, void* y_dev,
+                           void* stream);
+
 /* Synchronise the plan's device and report (and clear) any latched device-side
  * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, ...). */
 csar_status csar_plan_check(csar_plan plan);

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
-           "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward")
+           "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
+           "csar_G_noalloc")
 
 
 def _load() -> ctypes.CDLL:
@@ -75,11 +76,12 @@ def _load() -> ctypes.CDLL:
     lib.csar_af_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(Opts), i32, vp]
     lib.csar_af_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.csar_af_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.csar_G_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
                  "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
-                 "csar_af_solve", "csar_af_loss", "csar_af_backward"):
+                 "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -164,6 +166,19 @@ def csar_G(plan: Plan, x, y=None, stream=None):
     y = torch.empty_like(x) if y is None else y
     _need(y, torch.complex64, plan.n, "y")
     _check(lib.csar_G(plan.handle, _ptr(x), _ptr(y), _stream(stream)), "csar_G")
+    return y
+
+
+def csar_G_noalloc(geometry, x, y=None, stream=None):
+    """y = G(x) without a plan and without any device allocation by the library
+    (tables in a static device array; calls must not overlap on the GPU)."""
+    import torch
+    p = params_of(geometry)
+    n = p.n_az * p.n_rg
+    _need(x, torch.complex64, n, "x")
+    y = torch.empty_like(x) if y is None else y
+    _need(y, torch.complex64, n, "y")
+    _check(lib.csar_G_noalloc(ctypes.byref(p), _ptr(x), _ptr(y), _stream(stream)), "csar_G_noalloc")
     return y
 
 

@@ -69,6 +69,20 @@ PhaseCoef make_coef(double a, double b, double c, double sign) {
   return p;
 }
 
+csar_status validate(const csar_params* p) {
+  if (!p) return fail(CSAR_E_INVALID, "params is NULL");
+  if (!pow2_in(p->n_az, 16, 8192) || !pow2_in(p->n_rg, 16, 8192))
+    return fail(CSAR_E_INVALID, "n_az=%d n_rg=%d: each must be a power of two in [16, 8192]",
+                p->n_az, p->n_rg);
+  const double vals[] = {p->wavelength, p->velocity, p->r0, p->prf, p->bandwidth, p->pulse_len, p->fs};
+  const char* names[] = {"wavelength", "velocity", "r0", "prf", "bandwidth", "pulse_len", "fs"};
+  for (int i = 0; i < 7; ++i)
+    if (!(vals[i] > 0.0) || !std::isfinite(vals[i]))
+      return fail(CSAR_E_INVALID, "%s must be finite and > 0", names[i]);
+  if (p->c < 0.0 || !std::isfinite(p->c)) return fail(CSAR_E_INVALID, "c must be >= 0");
+  return CSAR_OK;
+}
+
 struct Buffers {
   float2* z = nullptr;             // n: pass-to-pass array
   uint32_t* off[2] = {nullptr, nullptr};
@@ -126,57 +140,13 @@ struct GraphKey {
 
 }  // namespace
 
-struct csar_plan_s {
-  csar_params p{};
-  int dev = 0;
-  int na = 0, nr = 0;
-  int64_t n = 0;
-  int col_p = 1, col_tile = 0, n_tiles = 0;
-  RowCoef* coef_g = nullptr;
-  RowCoef* coef_m = nullptr;
-  float2* tw = nullptr;
-  Buffers b;
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  GraphKey key[2];
-  bool use_graphs = true;
-};
-
-namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
-
-csar_status validate(const csar_params* p) {
-  if (!p) return fail(CSAR_E_INVALID, "params is NULL");
-  if (!pow2_in(p->n_az, 16, 8192) || !pow2_in(p->n_rg, 16, 8192))
-    return fail(CSAR_E_INVALID, "n_az=%d n_rg=%d: each must be a power of two in [16, 8192]",
-                p->n_az, p->n_rg);
-  const double vals[] = {p->wavelength, p->velocity, p->r0, p->prf, p->bandwidth, p->pulse_len, p->fs};
-  const char* names[] = {"wavelength", "velocity", "r0", "prf", "bandwidth", "pulse_len", "fs"};
-  for (int i = 0; i < 7; ++i)
-    if (!(vals[i] > 0.0) || !std::isfinite(vals[i]))
-      return fail(CSAR_E_INVALID, "%s must be finite and > 0", names[i]);
-  if (p->c < 0.0 || !std::isfinite(p->c)) return fail(CSAR_E_INVALID, "c must be >= 0");
-  return CSAR_OK;
-}
-
+namespace csar {
 // Per-row coefficients (cycles) of the three chirp-scaling phases; see phase.cuh.
 //   H1 = exp{j pi K_m (1/D - 1)(tau - 2 R_ref/(c D))^2},      tau - 2R_ref/c = j'/fs
 //   H2 = exp{j pi (D/K_m) f_tau^2} exp{j 4 pi f_tau R_ref (1/D - 1)/c},  f_tau = m fs/N_r
 //   H3 = exp{j 4 pi R0 f0 D/c} exp{-j 4 pi (K_m/c^2)(1 - D)((R0 - R_ref)/D)^2},
 //        R0 = R_ref + j' c/(2 fs)
-csar_status build_coefs(const csar_params& p, std::vector<RowCoef>& g, std::vector<RowCoef>& m) {
+csar_status build_coefs_into(const csar_params& p, RowCoef* g, RowCoef* m) {
   const double c = p.c > 0.0 ? p.c : 299792458.0;
   const double f0 = c / p.wavelength;
   const double kr = p.bandwidth / p.pulse_len;
@@ -185,8 +155,6 @@ csar_status build_coefs(const csar_params& p, std::vector<RowCoef>& g, std::vect
   const int na = p.n_az, nr = p.n_rg;
   const double jmax = nr / 2.0;  // |j'|, |m| <= N_r/2
   const double lim = 4194304.0;  // 2^22
-  g.resize(na);
-  m.resize(na);
   for (int k = 0; k < na; ++k) {
     const int ks = k < na / 2 ? k : k - na;
     const double fe = ks * p.prf / na;
@@ -220,6 +188,55 @@ csar_status build_coefs(const csar_params& p, std::vector<RowCoef>& g, std::vect
   }
   return CSAR_OK;
 }
+
+
+// Twiddle table W_8192^m, two levels (kTwLo + kTwHi entries), FP64 then rounded once.
+void build_twiddles(float2* tw) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < kTwLo; ++m) {
+    const double a = two_pi * m / kTwN;
+    tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  for (int h = 0; h < kTwHi; ++h) {
+    const double a = two_pi * (double)(h * kTwLo) / kTwN;
+    tw[kTwLo + h] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+}
+
+csar_status validate_params(const csar_params* p) { return validate(p); }
+csar_status set_error(csar_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace csar
+
+struct csar_plan_s {
+  csar_params p{};
+  int dev = 0;
+  int na = 0, nr = 0;
+  int64_t n = 0;
+  int col_p = 1, col_tile = 0, n_tiles = 0;
+  RowCoef* coef_g = nullptr;
+  RowCoef* coef_m = nullptr;
+  float2* tw = nullptr;
+  Buffers b;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  GraphKey key[2];
+  bool use_graphs = true;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -632,8 +649,8 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   *out = nullptr;
   if (flags != 0) return fail(CSAR_E_INVALID, "flags must be 0");
   if (csar_status st = validate(params)) return st;
-  std::vector<RowCoef> cg, cm;
-  if (csar_status st = build_coefs(*params, cg, cm)) return st;
+  std::vector<RowCoef> cg(params->n_az), cm(params->n_az);
+  if (csar_status st = build_coefs_into(*params, cg.data(), cm.data())) return st;
   int dev = 0;
   CK(cudaGetDevice(&dev));
   csar_plan plan = new csar_plan_s();
@@ -665,15 +682,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(cudaMemcpy(plan->coef_m, cm.data(), cm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
   {
     std::vector<float2> tw(kTwLo + kTwHi);
-    const double two_pi = 6.283185307179586476925286766559;
-    for (int m = 0; m < kTwLo; ++m) {
-      const double a = two_pi * m / kTwN;
-      tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
-    }
-    for (int h = 0; h < kTwHi; ++h) {
-      const double a = two_pi * (double)(h * kTwLo) / kTwN;
-      tw[kTwLo + h] = make_float2((float)std::cos(a), (float)-std::sin(a));
-    }
+    build_twiddles(tw.data());
     PK(dalloc(&plan->tw, tw.size()));
     PK(cudaMemcpy(plan->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
   }

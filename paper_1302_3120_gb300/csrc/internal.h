@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/csar.h"
 #include "fft.cuh"
 #include "phase.cuh"
 
@@ -126,6 +127,12 @@ __host__ __device__ constexpr int row_threads(int n) { return n * row_w(n) / reg
 constexpr int kDirectCols = 16;
 constexpr int kDirectMaxEntries = 128;
 constexpr int kDirectRows = 256;   // smallest N_a the direct DFT handles
+
+// ---------------------------------------------------------------- host helpers (csar_plan.cu)
+csar_status validate_params(const csar_params* p);
+csar_status build_coefs_into(const csar_params& p, RowCoef* g, RowCoef* m);
+void build_twiddles(float2* tw);
+csar_status set_error(csar_status st, const char* msg);
 
 // ---------------------------------------------------------------- launchers
 bool col_cluster_ok(int na, int p);
