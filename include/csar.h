@@ -76,6 +76,11 @@ typedef struct {
 } csar_params;
 
 typedef struct csar_plan_s* csar_plan;
+typedef struct csar_batch_s* csar_batch;
+
+/* csar_plan_create flags: force the column-pass cluster size (CTAs per column tile,
+ * 1..16, power of two; 0 = the autotuned or default choice). */
+#define CSAR_PLAN_COL_CLUSTER(p) ((uint32_t)(p) << 8)
 
 enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };
 enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1 };
@@ -201,6 +206,32 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
  * then the three passes). */
 csar_status csar_G_noalloc(const csar_params* params, const void* x_dev, void* y_dev,
                            void* stream);
+
+/* ---- Batches of independent patches (uneven sizes) -------------------------------- */
+
+/* One plan per patch (params[0..n_patches-1], each as for csar_plan_create with
+ * `flags`).  Not thread-safe; the batch owns the plans. */
+csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint32_t flags,
+                              csar_batch* out);
+csar_status csar_batch_destroy(csar_batch batch);
+
+/* Algorithm 1 on every patch together from X = 0: per iteration ONE CUDA graph launch
+ * on `stream`, whose parallel branches are the patches' pass sequences, so patches of
+ * different sizes run concurrently.  Y_dev, mask_dev, X_dev: host arrays of per-patch
+ * device pointers (layout as csar_solve); K: per-patch sparsity; opts: shared step,
+ * threshold and iteration count (opts->K ignored). */
+csar_status csar_solve_batched(csar_batch batch, const void* const* Y_dev,
+                               const uint32_t* const* mask_dev, void* const* X_dev,
+                               const int64_t* K, const csar_opts* opts, void* stream);
+
+/* csar_plan_check on every patch of the batch. */
+csar_status csar_batch_check(csar_batch batch);
+
+/* Autotuner: times `iters` ITA iterations on synthetic data for every column-pass
+ * cluster size available for (n_az, n_rg), keeps the fastest for plans created
+ * afterwards in this process (and in the file named by CSAR_TUNE_FILE, if set), and
+ * returns it in *chosen_cluster.  Synchronises the device; allocates temporaries. */
+csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster);
 
 /* Synchronise the plan's device and report (and clear) any latched device-side
  * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, ...). */

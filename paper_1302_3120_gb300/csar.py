@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
 EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
-           "csar_G_noalloc")
+           "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
+           "csar_batch_check", "csar_autotune")
 
 
 def _load() -> ctypes.CDLL:
@@ -77,11 +78,19 @@ def _load() -> ctypes.CDLL:
     lib.csar_af_loss.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.csar_af_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.csar_G_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp]
+    lib.csar_batch_create.argtypes = [ctypes.POINTER(Params), i32, u32, ctypes.POINTER(vp)]
+    lib.csar_batch_destroy.argtypes = [vp]
+    lib.csar_solve_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(Opts), vp]
+    lib.csar_batch_check.argtypes = [vp]
+    lib.csar_autotune.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(i32)]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
                  "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
-                 "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc"):
+                 "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc",
+                 "csar_batch_create", "csar_batch_destroy", "csar_solve_batched", "csar_batch_check",
+                 "csar_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -369,3 +378,69 @@ def autofocus_loss(plan: Plan, Y, mask_bits, theta, K: int, iters: int, mu: floa
     ITAUnroll, AutofocusLoss = _autograd()
     X = ITAUnroll.apply(theta, plan, Y, mask_bits, K, iters, mu)
     return AutofocusLoss.apply(X, theta, plan, Y, mask_bits)
+
+
+# ----------------------------------------------------------------------------- batches
+
+class Batch:
+    """Owns a csar_batch handle (one plan per patch)."""
+
+    def __init__(self, handle: int, shapes):
+        self.handle = ctypes.c_void_p(handle)
+        self.shapes = list(shapes)
+
+    def close(self) -> None:
+        if self.handle:
+            lib.csar_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def csar_batch_create(geometries, flags: int = 0) -> Batch:
+    arr = (Params * len(geometries))(*[params_of(g) for g in geometries])
+    h = ctypes.c_void_p()
+    _check(lib.csar_batch_create(arr, len(geometries), flags, ctypes.byref(h)), "csar_batch_create")
+    return Batch(h.value, [(g.n_az, g.n_rg) for g in geometries])
+
+
+def csar_solve_batched(batch: Batch, Ys, masks, Ks, iters: int, mu_mode="fixed", mu: float = 1.0,
+                       thresh="soft", Xs=None, stream=None):
+    """Algorithm 1 on every patch together (one graph launch per iteration)."""
+    import torch
+    n = len(batch.shapes)
+    Xs = [torch.empty_like(y) for y in Ys] if Xs is None else Xs
+    for i, (na, nr) in enumerate(batch.shapes):
+        _need(Ys[i], torch.complex64, na * nr, f"Y[{i}]")
+        _need(masks[i], torch.int32, na * nr // 32, f"mask[{i}]")
+        _need(Xs[i], torch.complex64, na * nr, f"X[{i}]")
+    vpa = ctypes.c_void_p * n
+    ys = vpa(*[y.data_ptr() for y in Ys])
+    ms = vpa(*[m.data_ptr() for m in masks])
+    xs = vpa(*[x.data_ptr() for x in Xs])
+    ks = (ctypes.c_int64 * n)(*[int(k) for k in Ks])
+    o = _opts(0, iters, mu_mode, mu, thresh)
+    _check(lib.csar_solve_batched(batch.handle, ys, ms, xs, ks, ctypes.byref(o), _stream(stream)),
+           "csar_solve_batched")
+    return Xs
+
+
+def csar_batch_check(batch: Batch) -> None:
+    _check(lib.csar_batch_check(batch.handle), "csar_batch_check")
+
+
+def csar_autotune(geometry, iters: int = 10) -> int:
+    """Time every column-pass cluster size for this shape; later plans use the fastest."""
+    p = params_of(geometry)
+    out = ctypes.c_int32(0)
+    _check(lib.csar_autotune(ctypes.byref(p), int(iters), ctypes.byref(out)), "csar_autotune")
+    return int(out.value)
+
+
+def plan_col_cluster(p: int) -> int:
+    """csar_plan_create flag forcing the column-pass cluster size."""
+    return int(p) << 8

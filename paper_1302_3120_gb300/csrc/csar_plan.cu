@@ -17,6 +17,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/csar.h"
@@ -207,6 +209,43 @@ csar_status validate_params(const csar_params* p) { return validate(p); }
 csar_status set_error(csar_status st, const char* msg) { return fail(st, "%s", msg); }
 }  // namespace csar
 
+// Column-pass cluster size chosen by csar_autotune, per (N_a, N_r), for plans created
+// afterwards in this process (optionally persisted in the file named by CSAR_TUNE_FILE).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("CSAR_TUNE_FILE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  int na, nr, p;
+  while (std::fscanf(fp, "%d %d %d", &na, &nr, &p) == 3)
+    if (col_cluster_ok(na, p)) g_tune[{na, nr}] = p;
+  std::fclose(fp);
+}
+
+void tune_save_locked() {
+  const char* f = std::getenv("CSAR_TUNE_FILE");
+  if (!f) return;
+  FILE* fp = std::fopen(f, "w");
+  if (!fp) return;
+  for (const auto& kv : g_tune) std::fprintf(fp, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+  std::fclose(fp);
+}
+
+int tuned_cluster(int na, int nr) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find({na, nr});
+  return it == g_tune.end() ? 0 : it->second;
+}
+}  // namespace
+
 struct csar_plan_s {
   csar_params p{};
   int dev = 0;
@@ -221,6 +260,21 @@ struct csar_plan_s {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   GraphKey key[2];
   bool use_graphs = true;
+};
+
+// A batch of independent patches: one plan per patch; each ITA iteration of the whole
+// batch is one CUDA graph whose parallel branches are the patches' kernel sequences.
+struct csar_batch_s {
+  std::vector<csar_plan> plans;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<const void*> key_y;
+  std::vector<int64_t> key_k;
+  csar_opts key_o{};
+  int dev = 0;
 };
 
 namespace {
@@ -457,6 +511,19 @@ __global__ void k_ctl_init(Ctl* c, uint32_t nx_from_list, const uint32_t* off0, 
   *c = z;
 }
 
+// Deterministic synthetic echo and 50% mask for the autotuner (hash of the index).
+__global__ void k_fill_synthetic(float2* y, uint32_t* mask, long long n, uint32_t seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    y[i] = make_float2((float)(h & 0xffff) / 65536.f - 0.5f, (float)(h >> 16) / 65536.f - 0.5f);
+    if ((i & 31) == 0) mask[i >> 5] = h * 3266489917u;
+  }
+}
+
 csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
   if (!o) return fail(CSAR_E_INVALID, "opts is NULL");
   if (o->K < 0) return fail(CSAR_E_INVALID, "K must be >= 0");
@@ -647,7 +714,11 @@ int32_t csar_version(void) { return 10000; }
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (flags != 0) return fail(CSAR_E_INVALID, "flags must be 0");
+  if (flags & ~0xff00u) return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
+  const int forced_p = (int)((flags >> 8) & 0xffu);
+  if (forced_p && params && !col_cluster_ok(params->n_az, forced_p))
+    return fail(CSAR_E_UNSUPPORTED, "column cluster size %d not available for n_az=%d", forced_p,
+                params->n_az);
   if (csar_status st = validate(params)) return st;
   std::vector<RowCoef> cg(params->n_az), cm(params->n_az);
   if (csar_status st = build_coefs_into(*params, cg.data(), cm.data())) return st;
@@ -659,7 +730,8 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->na = params->n_az;
   plan->nr = params->n_rg;
   plan->n = (int64_t)plan->na * plan->nr;
-  plan->col_p = col_cluster_default(plan->na);
+  plan->col_p = forced_p ? forced_p : tuned_cluster(plan->na, plan->nr);
+  if (!plan->col_p) plan->col_p = col_cluster_default(plan->na);
   plan->col_tile = col_w(plan->na, plan->col_p);
   plan->n_tiles = plan->nr / plan->col_tile;
   const char* ng = std::getenv("CSAR_NO_GRAPH");
@@ -901,6 +973,193 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
     CK(launch_af_axpy(b.af_bbar, b.af_h, mu, b.af_xbar, plan->n, s));
   }
   if (X0bar_dev) CK(cudaMemcpyAsync(X0bar_dev, b.af_xbar, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  return CSAR_OK;
+}
+
+// ---------------------------------------------------------------- batches
+csar_status csar_batch_destroy(csar_batch b);
+
+csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint32_t flags, csar_batch* out) {
+  if (!out) return fail(CSAR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!params || n_patches <= 0) return fail(CSAR_E_INVALID, "need n_patches > 0 parameter sets");
+  csar_batch b = new csar_batch_s();
+  CK(cudaGetDevice(&b->dev));
+  for (int i = 0; i < n_patches; ++i) {
+    csar_plan p = nullptr;
+    if (csar_status st = csar_plan_create(&params[i], flags, &p)) {
+      csar_batch_destroy(b);
+      return st;
+    }
+    b->plans.push_back(p);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      csar_batch_destroy(b);
+      return cuda_fail(ce, "csar_batch_create");
+    }
+    b->streams.push_back(s);
+    b->join.push_back(e);
+  }
+  cudaError_t ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    csar_batch_destroy(b);
+    return cuda_fail(ce, "csar_batch_create");
+  }
+  *out = b;
+  return CSAR_OK;
+}
+
+csar_status csar_batch_destroy(csar_batch b) {
+  if (!b) return CSAR_OK;
+  DeviceGuard dg(b->dev);
+  cudaDeviceSynchronize();
+  for (int i = 0; i < 2; ++i)
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (auto p : b->plans) csar_plan_destroy(p);
+  delete b;
+  return CSAR_OK;
+}
+
+csar_status csar_solve_batched(csar_batch b, const void* const* Y_dev, const uint32_t* const* mask_dev,
+                               void* const* X_dev, const int64_t* K, const csar_opts* opts, void* stream) {
+  if (!b) return fail(CSAR_E_INVALID, "batch is NULL");
+  if (!Y_dev || !mask_dev || !X_dev || !K || !opts) return fail(CSAR_E_INVALID, "null argument");
+  const int np = (int)b->plans.size();
+  DeviceGuard dg(b->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  csar_opts o = *opts;
+  for (int i = 0; i < np; ++i) {
+    o.K = K[i];
+    if (csar_status st = check_opts(b->plans[i], &o, true)) return st;
+    if (!Y_dev[i] || !mask_dev[i] || !X_dev[i]) return fail(CSAR_E_INVALID, "null data pointer (patch %d)", i);
+    if (csar_status st = ensure_capacity(b->plans[i], K[i], o.iters)) return st;
+  }
+  // per-solve set-up of every patch
+  for (int i = 0; i < np; ++i) {
+    csar_plan p = b->plans[i];
+    CK(prepare_inputs(p, (const float2*)Y_dev[i], mask_dev[i], s));
+    CK(cudaMemsetAsync(p->b.off[0], 0, (p->n_tiles + 1) * sizeof(uint32_t), s));
+    k_ctl_init<<<1, 1, 0, s>>>(p->b.ctl, 0u, p->b.off[0], p->n_tiles);
+    CK(cudaGetLastError());
+  }
+  // one graph per parity: fork to the patches' streams, one branch per patch, join
+  bool same = (int)b->key_y.size() == np && b->key_o.mu_mode == o.mu_mode && b->key_o.mu == o.mu &&
+              b->key_o.thresh == o.thresh;
+  for (int i = 0; same && i < np; ++i) same = b->key_y[i] == Y_dev[i] && b->key_k[i] == K[i];
+  if (!same) {
+    for (int par = 0; par < 2; ++par) {
+      if (b->exec[par]) cudaGraphExecDestroy(b->exec[par]);
+      b->exec[par] = nullptr;
+    }
+  }
+  for (int par = 0; par < 2 && o.iters > 0; ++par) {
+    if (b->exec[par]) continue;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->fork, b->cap);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      csar_opts oi = o;
+      oi.K = K[i];
+      e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+      if (e == cudaSuccess) e = enqueue_iteration(b->plans[i], (const float2*)Y_dev[i], par, oi, b->streams[i], nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->streams[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join[i], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e != cudaSuccess ? e : e2, "capture of the batched iteration");
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&b->exec[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaGraphInstantiate (batch)");
+  }
+  b->key_y.assign(Y_dev, Y_dev + np);
+  b->key_k.assign(K, K + np);
+  b->key_o = o;
+  int cur = 0;
+  for (int it = 0; it < o.iters; ++it) {
+    CK(cudaGraphLaunch(b->exec[cur], s));
+    cur = 1 - cur;
+  }
+  for (int i = 0; i < np; ++i) {
+    csar_plan p = b->plans[i];
+    CK(cudaMemsetAsync(X_dev[i], 0, (size_t)p->n * sizeof(float2), s));
+    CK(launch_list_to_dense(p->b.off[cur], p->b.idx[cur], p->b.val[cur], p->n_tiles, (float2*)X_dev[i], s));
+  }
+  return CSAR_OK;
+}
+
+csar_status csar_batch_check(csar_batch b) {
+  if (!b) return fail(CSAR_E_INVALID, "batch is NULL");
+  for (auto p : b->plans)
+    if (csar_status st = csar_plan_check(p)) return st;
+  return CSAR_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster) {
+  if (csar_status st = validate(params)) return st;
+  if (iters <= 0) return fail(CSAR_E_INVALID, "iters must be > 0");
+  const int na = params->n_az, nr = params->n_rg;
+  const size_t n = (size_t)na * nr;
+  float2* y = nullptr;
+  float2* x = nullptr;
+  uint32_t* m = nullptr;
+  CK(dalloc(&y, n));
+  CK(dalloc(&x, n));
+  CK(dalloc(&m, n / 32));
+  k_fill_synthetic<<<1024, 256, 0, 0>>>(y, m, (long long)n, 12345u);
+  CK(cudaGetLastError());
+  csar_opts o{};
+  o.K = std::max<int64_t>(1, (int64_t)(0.01 * (double)n));
+  o.iters = iters;
+  o.mu_mode = CSAR_MU_FIXED;
+  o.mu = 1.f;
+  o.thresh = CSAR_THRESH_SOFT;
+  int best_p = 0;
+  float best_ms = 0.f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int p = 1; p <= 16; p <<= 1) {
+    if (!col_cluster_ok(na, p)) continue;
+    csar_plan plan = nullptr;
+    if (csar_plan_create(params, CSAR_PLAN_COL_CLUSTER(p), &plan) != CSAR_OK) continue;
+    float ms = -1.f;
+    if (csar_solve(plan, y, m, x, &o, nullptr, nullptr) == CSAR_OK) {   // warm-up and capture
+      cudaEventRecord(e0, 0);
+      const csar_status st = csar_solve(plan, y, m, x, &o, nullptr, nullptr);
+      cudaEventRecord(e1, 0);
+      if (st == CSAR_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    csar_plan_destroy(plan);
+    if (ms > 0.f && (best_p == 0 || ms < best_ms)) {
+      best_p = p;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(y);
+  cudaFree(x);
+  cudaFree(m);
+  if (!best_p) return fail(CSAR_E_INTERNAL, "autotune: no column configuration ran");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    g_tune[{na, nr}] = best_p;
+    tune_save_locked();
+  }
+  if (chosen_cluster) *chosen_cluster = best_p;
   return CSAR_OK;
 }
 
