@@ -184,12 +184,120 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def _event_ms(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_batched(args, world, rank, local):
+    """64 airborne patches of uneven size (each axis from {512, 1024, 2048, 4096}), 1%
+    Rayleigh scenes, 50% sampling, K_p = 1% of each patch: iterations/s of the batched
+    solve (one graph launch per iteration) against the per-patch loop."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1302_3120_gb300 import build
+    build.build()
+    from paper_1302_3120_gb300 import csar
+    rng = np.random.default_rng(2024 + rank)
+    shapes = synth.batch_shapes(rng, 64)
+    geoms = [synth.airborne(a, r) for a, r in shapes]
+    Ys, Ms, Ks = [], [], []
+    for g in geoms:
+        plan = csar.csar_plan_create(g)
+        x = synth.sparse_rayleigh(rng, g.n_az, g.n_rg, 0.01).astype(np.complex64)
+        Ys.append(csar.csar_G(plan, torch.from_numpy(x).cuda()))
+        Ms.append(torch.from_numpy(synth.pack_mask(synth.bernoulli_mask(rng, g.n_az, g.n_rg, 0.5))
+                                   .view(np.int32)).cuda())
+        Ks.append(int(round(0.01 * g.n_az * g.n_rg)))
+        plan.close()
+    for g in {(a, r) for a, r in shapes}:
+        csar.csar_autotune(synth.airborne(*g), iters=3)
+    batch = csar.csar_batch_create(geoms)
+    plans = [csar.csar_plan_create(g) for g in geoms]
+    Xs = [torch.empty_like(y) for y in Ys]
+    stream = torch.cuda.current_stream()
+    csar.csar_solve_batched(batch, Ys, Ms, Ks, max(args.warmup, 3), Xs=Xs)
+    for i, p in enumerate(plans):
+        csar.csar_solve(p, Ys[i], Ms[i], Ks[i], max(args.warmup, 3), X=Xs[i])
+    steps = args.steps
+    with ClockSampler(local) as clk:
+        ms_b = _event_ms(lambda: csar.csar_solve_batched(batch, Ys, Ms, Ks, steps, Xs=Xs, stream=stream), stream)
+    ms_l = _event_ms(lambda: [csar.csar_solve(p, Ys[i], Ms[i], Ks[i], steps, X=Xs[i], stream=stream)
+                              for i, p in enumerate(plans)], stream)
+    csar.csar_batch_check(batch)
+    elems = sum(a * r for a, r in shapes)
+    line = {"metric": "batched ITA iterations/s (64 uneven airborne patches)", "value": steps / (ms_b / 1e3),
+            "unit": "iterations/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_b / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "64 patches, axes from {512,1024,2048,4096}, 1% Rayleigh, 50% mask, "
+                                   "K_p = 1% of each patch, fixed mu = 1, soft", "elements": elems,
+                       "shapes": shapes},
+            "per_patch_loop": {"value": steps / (ms_l / 1e3), "ms_per_step": ms_l / steps},
+            "speedup_vs_loop": ms_l / ms_b, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_autofocus(args, world, rank, local):
+    """4096^2 airborne, 0.5% scene, 50% sampling, theta = 3 sinusoids, K = 83886:
+    forward (50-iteration unroll with checkpoints) + loss + backward per step."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1302_3120_gb300 import build
+    build.build()
+    from paper_1302_3120_gb300 import csar
+    na = nr = 4096
+    g = synth.airborne(na, nr)
+    rng = np.random.default_rng(5 + rank)
+    x = synth.sparse_rayleigh(rng, na, nr, 0.005).astype(np.complex64)
+    th_true = synth.theta_sinusoids(rng, na)
+    mask = synth.bernoulli_mask(rng, na, nr, 0.5)
+    plan = csar.csar_plan_create(g)
+    yg = csar.csar_G(plan, torch.from_numpy(x).cuda())
+    Y = (yg * torch.from_numpy(np.exp(1j * th_true).astype(np.complex64)).cuda()[:, None]).contiguous()
+    md = torch.from_numpy(synth.pack_mask(mask).view(np.int32)).cuda()
+    theta = torch.from_numpy((th_true + 0.05 * synth.theta_sinusoids(rng, na, peak=1.0)).astype(np.float32)).cuda()
+    K, iters = 83886, 50
+    stream = torch.cuda.current_stream()
+
+    def step():
+        th = theta.clone().requires_grad_(True)
+        L = csar.autofocus_loss(plan, Y, md, th, K, iters)
+        L.backward()
+        return L
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    steps = max(1, min(args.steps, 20))
+    fwd = _event_ms(lambda: csar.csar_af_solve(plan, Y, md, theta, K, iters), stream)
+    tot = _event_ms(lambda: [step() for _ in range(steps)], stream) / steps
+    line = {"metric": "autofocus forward+backward steps/s (4096^2, 50-iteration unroll)",
+            "value": 1e3 / tot, "unit": "steps/s", "n_gpus": world, "steps": steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": tot, "forward_ms": fwd,
+            "forward_iterations_per_s": iters / (fwd / 1e3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "airborne 4096x4096, 0.5% Rayleigh, 50% mask, theta = 3 sinusoids "
+                                   "(peak 2 pi), K = 83886, 50 iterations, soft, mu = 1"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="spaceborne8192",
+                    choices=["spaceborne8192", "batched", "autofocus"],
+                    help="spaceborne8192 (default, the headline) or the batched / autofocus rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--size", type=int, default=8192,
@@ -206,6 +314,12 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
+        return
+    if args.workload == "autofocus":
+        run_autofocus(args, world, rank, local)
         return
 
     import torch
