@@ -72,21 +72,81 @@ __device__ __forceinline__ void cluster_barrier() {
   if constexpr (P > 1) cg::this_cluster().sync();
 }
 
-// Address of element index e of column w in the shared buffer of CTA `rank`.
-template <int N, int P>
-__device__ __forceinline__ float2* peer_slot(float2* sm, int rank, int w, int e) {
-  using C = ColCfg<N, P>;
-  float2* p = sm + Layout<C::Q, C::W, true>::template at<4>(w, e);
-  if constexpr (C::P > 1) return cg::this_cluster().map_shared_rank(p, rank);
-  return p;
+// ---------------------------------------------------------------- cluster exchanges
+// The cross-CTA steps move data with plain remote stores into the peers' shared memory
+// and signal with single-use mbarriers (one per exchange, P arrivals each) instead of
+// full cluster barriers: after a CTA-wide __syncthreads, thread k alone performs a
+// release arrive (cluster scope) on the mbarrier of CTA k, and every thread waits on its
+// own mbarrier with acquire semantics.  Only P threads per CTA execute a cluster-scope
+// release, and loads issued before the wait are not held back by it.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 x) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.x), "f"(x.y) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the local mbarrier at `a`, for one second at most: a peer
+// that never signals makes the kernel latch kErrTimeout and go on (no endless spin).
+__device__ __forceinline__ void mbar_wait(uint32_t a, uint32_t parity, Ctl* ctl) {
+  if (mbar_test(a, parity)) return;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_test(a, parity)) return;
+    if (global_ns() - t0 > 1000000000ull) {
+      if (ctl) atomicOr(&ctl->err, kErrTimeout);
+      return;
+    }
+  }
+}
+// Signal on mbarrier `mb` (local address; the same offset in every CTA) of all P CTAs
+// that this CTA's prior shared-memory work (remote stores, or reads of its own buffer)
+// is complete.
+template <int P>
+__device__ __forceinline__ void xch_signal(uint32_t mb) {
+  __syncthreads();
+  if (threadIdx.x < P) mbar_arrive_cluster(cluster_map(mb, (int)threadIdx.x));
+}
+
+// Mbarriers of the column pass (single use, phase 0, P arrivals each).
+enum : int { kMbBs = 0, kMbFree = 1, kMbSb = 2, kMbCount = 4 };
 
 // Cross-CTA step of the blocked-in transform: v holds, per i < RP, the P values
 // n1 = 0..P-1 of n2 = c*Q/P + t + QR*i; their length-P DFT (times W_N^(n2 k1)) is
 // pushed to element n2 of CTA k1.  Then the canonical input of the local FFT is read.
+// The twiddles W_N^(n2 k1) are W^(n2 k1) = w1^k1 (w1 = W^n2 from the table) within
+// each group of four k1, re-anchored from the table at every multiple of four.
 template <int N, int P, bool INV>
 __device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* sm, const float2* tw,
-                                         int c, int t, int w) {
+                                         int c, int t, int w, const uint32_t (&peer)[P],
+                                         uint32_t mb, Ctl* ctl) {
   using C = ColCfg<N, P>;
   using L = Layout<C::Q, C::W, true>;
   if constexpr (C::P > 1) {
@@ -97,13 +157,23 @@ __device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* s
 #pragma unroll
       for (int n1 = 0; n1 < C::P; ++n1) a[n1] = v[i * C::P + n1];
       Dft<C::P, INV>::run(a);
+      const float2 w1 = twiddle_tab<INV>(tw, n2 * (kTwN / N));
+      float2 wp[4];
+      wp[0] = make_float2(1.f, 0.f);
+      wp[1] = w1;
+      wp[2] = cmul(w1, w1);
+      wp[3] = cmul(wp[2], w1);
+      const uint32_t off = 8u * (uint32_t)L::template at<4>(w, n2);
+      float2 anc = wp[0];
 #pragma unroll
       for (int k1 = 0; k1 < C::P; ++k1) {
-        const float2 x = k1 ? cmul(a[k1], twiddle_tab<INV>(tw, n2 * k1 * (kTwN / N))) : a[k1];
-        *peer_slot<N, P>(sm, k1, w, n2) = x;
+        if (k1 >= 4 && k1 % 4 == 0) anc = twiddle_tab<INV>(tw, n2 * k1 * (kTwN / N));
+        const float2 tk = (k1 % 4 == 0) ? anc : (k1 < 4 ? wp[k1] : cmul(anc, wp[k1 % 4]));
+        st_cluster(peer[k1] + off, k1 ? cmul(a[k1], tk) : a[k1]);
       }
     }
-    cluster_barrier<C::P>();
+    xch_signal<C::P>(mb);
+    mbar_wait(mb, 0u, ctl);
 #pragma unroll
     for (int s = 0; s < C::R; ++s) v[s] = sm[L::template at<4>(w, t + s * C::QR)];
   }
@@ -138,7 +208,8 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
   float2* sm = smem;
   float2* tw = smem + L::kSmemElems;
   float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);   // 32 floats
-  uint32_t* hist = reinterpret_cast<uint32_t*>(red + 32);      // kHistBins (SELECT)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(red + 32);      // kMbCount mbarriers
+  uint32_t* hist = reinterpret_cast<uint32_t*>(mbar + kMbCount);  // kHistBins (SELECT)
 
   if constexpr (MODE == COL_REPASS) {
     if (a.ctl->need_repass == 0) return;   // uniform for the whole grid
@@ -146,27 +217,44 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
   if (a.gate && *a.gate != a.gate_val) return;
   const int c = (P > 1) ? (int)(blockIdx.x % P) : 0;      // rank in the cluster
   const int tile = blockIdx.x / P;
+  if constexpr (MODE == COL_SPARSE_FWD) {
+    // groups of kDirectCols columns with few entries are transformed by k_sparse_dft;
+    // the test is uniform per cluster (one tile), so whole clusters leave together
+    const int bpg = kDirectCols / W > 0 ? kDirectCols / W : 1;
+    const int grp = (tile * W) / kDirectCols;
+    const uint32_t ge = a.xs_off[(grp + 1) * bpg < a.nr / W ? (grp + 1) * bpg : a.nr / W] -
+                        a.xs_off[grp * bpg];
+    if (N >= kDirectRows && ge <= (uint32_t)kDirectMaxEntries) return;
+  }
   load_twiddles(tw, a.tw);
   const int tid = threadIdx.x;
   const int w = tid % W, t = tid / W;
   const int col = tile * W + w;
   const size_t nr = (size_t)a.nr;
   float2 v[R];
-  // every CTA of the cluster is running before any remote store (no memory ordering)
+  // sampling bits of this thread's R rows (pre-transposed: bit s <-> strided row s),
+  // fetched first so the load is long complete when the mask is applied
+  uint32_t mbits = 0u;
+  if constexpr (MODE == COL_RESID || MODE == COL_NORM) mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
+  // exchange mbarriers, then every CTA of the cluster is running (and its mbarriers are
+  // initialised) before any remote store or arrive
+  const uint32_t mb0 = smem_addr(mbar);
+  uint32_t peer[P];
   if constexpr (P > 1) {
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) mbar_init(mb0 + 8u * j, (uint32_t)P);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) peer[k] = cluster_map(smem_addr(sm), k);
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  } else {
+    peer[0] = smem_addr(sm);
   }
 
   // ------------------------------------------------------------------ input
   if constexpr (MODE == COL_SPARSE_FWD) {
-    {
-      // groups of kDirectCols columns with few entries are transformed by k_sparse_dft
-      const int bpg = kDirectCols / W > 0 ? kDirectCols / W : 1;
-      const int grp = (tile * W) / kDirectCols;
-      const uint32_t ge = a.xs_off[(grp + 1) * bpg < a.nr / W ? (grp + 1) * bpg : a.nr / W] -
-                          a.xs_off[grp * bpg];
-      if (N >= kDirectRows && ge <= (uint32_t)kDirectMaxEntries) return;   // uniform per cluster
-    }
     // zero tile; entries whose row belongs to this CTA's blocked input set
     for (int i = tid; i < L::kSmemElems; i += NT) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -189,21 +277,34 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     for (int s = 0; s < R; ++s) v[s] = sm[L::template at<4>(w, t + QR * s)];
     // the buffer is reused by the cross step: peers push into it only after every CTA of
     // the cluster has read its staged input
-    if constexpr (P > 1) cluster_barrier<P>();
-    else __syncthreads();
+    if constexpr (P > 1) {
+      xch_signal<P>(mb0 + 8u * kMbFree);
+      mbar_wait(mb0 + 8u * kMbFree, 0u, a.ctl);
+    } else {
+      __syncthreads();
+    }
   } else {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P>(c, t, s) * nr + col]);
   }
+  // selection passes: the support range of this tile, its first entry per thread and the
+  // candidate cut are fetched while the column loads are in flight
+  uint32_t sel_e0 = 0u, sel_e1 = 0u, sel_idx = 0u, sel_cut = 0u;
+  if constexpr (MODE == COL_SELECT || MODE == COL_REPASS) {
+    sel_e0 = a.xs_off[tile];
+    sel_e1 = a.xs_off[tile + 1];
+    sel_cut = a.ctl->cut_key;
+    if (sel_e0 + tid < sel_e1) sel_idx = a.xs_idx[sel_e0 + tid];
+  }
 
   // ------------------------------------------------------------------ transforms
   if constexpr (MODE == COL_FWD || MODE == COL_SPARSE_FWD) {
-    bs_cross<N, P, false>(v, sm, tw, c, t, w);
+    bs_cross<N, P, false>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, false, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
     for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], v[s]);
   } else if constexpr (MODE == COL_INV) {
-    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
     for (int s = 0; s < R; ++s)
@@ -212,51 +313,89 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     // F_a r = F_a(S.Y) - F_a(S.g): the transformed masked echo (a.y) is subtracted
     // at the store, so only the mask bits stay live between the two transforms;
     // ||r||^2 follows from Parseval, sum |F_a r|^2 / N_a.
-    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
-    {
-      // sampling bits of this thread's R rows, pre-transposed: bit s <-> strided row s
-      const uint32_t mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
 #pragma unroll
-      for (int s = 0; s < R; ++s)
-        v[s] = ((mbits >> s) & 1u) ? cscale(v[s], a.scale) : make_float2(0.f, 0.f);
-    }
+    for (int s = 0; s < R; ++s)
+      v[s] = ((mbits >> s) & 1u) ? cscale(v[s], a.scale) : make_float2(0.f, 0.f);
     fft<Q, false, L, true, R>(v, sm, tw, t, w);
     float acc = 0.f;
     bool bad = false;
+    // The values of F_a(S.Y) are loaded in groups before any of them is used, so their
+    // latencies overlap (a load between two stores would wait for the previous store).
     if constexpr (P == 1) {
+      constexpr int kG = R / 4;
 #pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const size_t idx = (size_t)(t + s * QR) * nr + col;
-        const float2 r = csub(__ldcs(&a.y[idx]), v[s]);
-        bad |= !(isfinite(r.x) && isfinite(r.y));
-        acc += cabs2(r);
-        __stcs(&a.out[idx], r);
-      }
-    } else {
-      cluster_barrier<P>();   // every CTA has finished with its own buffer
+      for (int g0 = 0; g0 < R; g0 += kG) {
+        float2 yv[kG];
 #pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const int k2 = t + s * QR;
-        const float2 x = c ? cmul(v[s], twiddle_tab<false>(tw, c * k2 * (kTwN / N))) : v[s];
-        const int dst = k2 / (Q / P), k2l = k2 % (Q / P);
-        *peer_slot<N, P>(sm, dst, w, k2l * P + c) = x;
-      }
-      cluster_barrier<P>();
+        for (int s = 0; s < kG; ++s) yv[s] = __ldcs(&a.y[(size_t)(t + (g0 + s) * QR) * nr + col]);
 #pragma unroll
-      for (int i = 0; i < C::RP; ++i) {
-        const int k2l = t + QR * i;
-        float2 b[P];
-#pragma unroll
-        for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, k2l * P + n1)];
-        Dft<P, false>::run(b);
-#pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) {
-          const size_t idx = (size_t)(c * (Q / P) + k2l + Q * k1) * nr + col;
-          const float2 r = csub(__ldcs(&a.y[idx]), b[k1]);
+        for (int s = 0; s < kG; ++s) {
+          const size_t idx = (size_t)(t + (g0 + s) * QR) * nr + col;
+          const float2 r = csub(yv[s], v[g0 + s]);
           bad |= !(isfinite(r.x) && isfinite(r.y));
           acc += cabs2(r);
           __stcs(&a.out[idx], r);
+        }
+      }
+    } else {
+      // SB step: twiddle W_N^(c k2) (k2 = t + s QR) and push k2 to CTA s / RP at element
+      // c*Q/P + k2l (source-major, so pushes and the final reads are conflict-free), once
+      // every CTA has finished reading its own buffer.  Twiddles: table anchors at every
+      // fourth s, steps W^(c QR u) in between.
+      xch_signal<P>(mb0 + 8u * kMbFree);
+      mbar_wait(mb0 + 8u * kMbFree, 0u, a.ctl);
+      {
+        float2 stp[4];
+        stp[0] = make_float2(1.f, 0.f);
+        stp[1] = twiddle_tab<false>(tw, c * QR * (kTwN / N));
+        stp[2] = cmul(stp[1], stp[1]);
+        stp[3] = cmul(stp[2], stp[1]);
+        float2 anc = stp[0];
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+          if (s % 4 == 0) anc = twiddle_tab<false>(tw, c * (t + s * QR) * (kTwN / N));
+          const float2 x = c ? cmul(v[s], (s % 4 == 0) ? anc : cmul(anc, stp[s % 4])) : v[s];
+          const int dst = s / C::RP, k2l = t + QR * (s % C::RP);
+          st_cluster(peer[dst] + 8u * (uint32_t)L::template at<4>(w, c * (Q / P) + k2l), x);
+        }
+      }
+      xch_signal<P>(mb0 + 8u * kMbSb);
+      // v is dead here: its registers receive this thread's values of F_a(S.Y) (in two
+      // groups), so the loads of the first group overlap the wait
+      constexpr int kGI = C::RP >= 2 ? C::RP / 2 : 1;   // i-values per group
+      const float2* yc = a.y + (size_t)(c * (Q / P) + t) * nr + col;
+      float2* oc = a.out + (size_t)(c * (Q / P) + t) * nr + col;
+      const size_t di = (size_t)QR * nr, dk = (size_t)Q * nr;
+      float2 yv[kGI * P];
+#pragma unroll
+      for (int i = 0; i < kGI; ++i)
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) yv[i * P + k1] = __ldcs(yc + i * di + k1 * dk);
+      mbar_wait(mb0 + 8u * kMbSb, 0u, a.ctl);
+#pragma unroll
+      for (int i0 = 0; i0 < C::RP; i0 += kGI) {
+        if (i0 > 0) {
+#pragma unroll
+          for (int i = 0; i < kGI; ++i)
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) yv[i * P + k1] = __ldcs(yc + (i0 + i) * di + k1 * dk);
+        }
+#pragma unroll
+        for (int i = 0; i < kGI; ++i) {
+          const int k2l = t + QR * (i0 + i);
+          float2 b[P];
+#pragma unroll
+          for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, n1 * (Q / P) + k2l)];
+          Dft<P, false>::run(b);
+#pragma unroll
+          for (int k1 = 0; k1 < P; ++k1) {
+            const float2 r = csub(yv[i * P + k1], b[k1]);
+            bad |= !(isfinite(r.x) && isfinite(r.y));
+            acc += cabs2(r);
+            __stcs(oc + (i0 + i) * di + k1 * dk, r);
+          }
         }
       }
     }
@@ -264,9 +403,8 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     const float tot = block_sum<NT>(acc, red);
     if (tid == 0) a.partial[blockIdx.x] = tot * a.scale;
   } else if constexpr (MODE == COL_NORM) {
-    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
-    const uint32_t mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
     float acc = 0.f;
 #pragma unroll
     for (int s = 0; s < R; ++s) acc += ((mbits >> s) & 1u) ? cabs2(cscale(v[s], a.scale)) : 0.f;
@@ -277,7 +415,7 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     if constexpr (HIST) {
       for (int i = tid; i < (int)kHistBins; i += NT) hist[i] = 0u;
     }
-    bs_cross<N, P, true>(v, sm, tw, c, t, w);
+    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
     __syncthreads();
     // local element m of this CTA is global row c + P*m
@@ -285,9 +423,9 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     for (int s = 0; s < R; ++s) sm[L::template at<4>(w, t + s * QR)] = cscale(v[s], a.scale);
     __syncthreads();
     // support of the current iterate: record Delta X there, exclude from candidates
-    const uint32_t e0 = a.xs_off[tile], e1 = a.xs_off[tile + 1];
-    for (uint32_t e = e0 + tid; e < e1; e += NT) {
-      const uint32_t idx = a.xs_idx[e];
+    for (uint32_t e = sel_e0 + tid; e < sel_e1; e += NT) {
+      const uint32_t idx = sel_idx;
+      if (e + NT < sel_e1) sel_idx = a.xs_idx[e + NT];
       const int row = (int)(idx / (uint32_t)a.nr);
       if (P > 1 && row % P != c) continue;
       const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
@@ -296,7 +434,7 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
       sm[p] = make_float2(__int_as_float(0x7fffffff), 0.f);
     }
     __syncthreads();
-    const uint32_t cut = a.ctl->cut_key;
+    const uint32_t cut = sel_cut;
     constexpr uint32_t full = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
     const int lane = tid & 31;
 #pragma unroll
@@ -363,7 +501,7 @@ static size_t col_smem(int mode) {
   using C = ColCfg<N, P>;
   using L = Layout<C::Q, C::W, true>;
   size_t b = (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
-             32 * sizeof(float);
+             32 * sizeof(float) + kMbCount * sizeof(uint64_t);
   if (mode == COL_SELECT) b += kHistBins * sizeof(uint32_t);
   return b;
 }

@@ -591,6 +591,8 @@ csar_status latched(csar_plan plan) {
     if (c.err & kErrNonfinite) return fail(CSAR_E_NONFINITE, "non-finite value in the echo or iterate");
     if (c.err & kErrCapacity)
       return fail(CSAR_E_INTERNAL, "selection candidate capacity exceeded (degenerate magnitudes)");
+    if (c.err & kErrTimeout)
+      return fail(CSAR_E_TIMEOUT, "a column-pass cluster exchange timed out (a peer CTA never signalled)");
     return fail(CSAR_E_INTERNAL, "device error bits 0x%x", c.err);
   }
   return CSAR_OK;

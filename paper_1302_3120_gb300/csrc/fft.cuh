@@ -147,6 +147,7 @@ __host__ __device__ constexpr int first_radix(int q, int r) {
 // SHIFT: one padding slot every 2^SHIFT elements.
 template <int Q, int W, bool COL>
 struct Layout {
+  static constexpr int kW = W;
   static constexpr int kStride = COL ? W : 1;   // flat distance between n and n+1
   static __device__ __forceinline__ int flat(int w, int n) { return COL ? n * W + w : w * Q + n; }
   template <int SHIFT>
@@ -177,6 +178,25 @@ template <bool COL, int RS>
 struct PadShift {
   static constexpr int value = (!COL && RS == 32) ? 5 : 4;
 };
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// First exchange of a column layout (written by the first stage, radix RS0, read by
+// the second, radix RS1).  The first stage writes elements RS0*b + r, which puts the
+// W columns of 16/W consecutive butterflies b on the same banks; instead of padding,
+// the r-field of the flat index f = n*W + w is XORed with the low bits of b:
+//     slot(f) = f ^ (W * ((f >> log2(W*RS0)) & M)),   M = min(16/W, RS0) - 1,
+// a permutation inside each group of RS0 rows.  Both the write (per-thread base, M+1
+// address registers, compile-time offsets) and the second-stage read (per-thread
+// base, affine in r) stay free of per-element address arithmetic.
+template <int Q, int W, int RS0, int RS1>
+struct Swz {
+  static constexpr int M = ((16 / W) < RS0 ? (16 / W) : RS0) - 1;
+  static constexpr int kShift = ilog2(W * RS0);
+  static constexpr bool kOn = M > 0 && RS0 > 1 && (Q / (RS0 * RS1)) % (M + 1) == 0;
+  static __device__ __forceinline__ int slot(int f) { return kOn ? (f ^ (W * ((f >> kShift) & M))) : f; }
+};
+constexpr int kSwzPad = -1;   // PS / OPS value marking the swizzled first exchange
 
 template <int RS, bool INV>
 __device__ __forceinline__ void apply_twiddles(float2* a, const float2* tw, int step) {
@@ -217,7 +237,18 @@ struct Stages {
     constexpr int RS = (NS == 1) ? first_radix(Q, R) : R;
     constexpr int G = R / RS;             // butterflies per thread
     constexpr int QR = Q / R;             // threads per transform
-    if constexpr (NS > 1) {
+    if constexpr (NS > 1 && PS == kSwzPad) {
+      // second stage of a column transform: read the swizzled first exchange
+      using S = Swz<Q, L::kW, NS, RS>;
+      __syncthreads();
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int b = t + g * QR;
+        const int ba = S::slot(L::flat(w, b));   // the XOR term does not depend on r
+#pragma unroll
+        for (int r = 0; r < RS; ++r) v[g + r * G] = sm[ba + r * (Q / RS) * L::kStride];
+      }
+    } else if constexpr (NS > 1) {
       __syncthreads();
       using RD = Strided<L, PS, Q / RS>;
 #pragma unroll
@@ -243,17 +274,34 @@ struct Stages {
       for (int r = 0; r < RS; ++r) v[g + r * G] = a[r];
     }
     if constexpr (NS * RS < Q) {
-      constexpr int OPS = PadShift<COL, RS>::value;
+      using S = Swz<Q, L::kW, RS, (NS * RS < Q) ? R : 1>;
+      constexpr bool kSwz = COL && NS == 1 && S::kOn;
+      constexpr int OPS = kSwz ? kSwzPad : PadShift<COL, RS>::value;
       __syncthreads();
-      using WR = Strided<L, OPS, NS>;
+      if constexpr (kSwz) {
+        // element RS*b + r goes to slot (RS*b + (r ^ (b & M)))*W + w
+        constexpr int M = S::M;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int b = t + g * QR;
-        const int k = b & (NS - 1);
-        const int n0 = (b / NS) * NS * RS + k;
-        const int ba = WR::base(w, n0);
+        for (int g = 0; g < G; ++g) {
+          const int b = t + g * QR;
+          const int base = L::flat(w, RS * b);
+          int ad[M + 1];
 #pragma unroll
-        for (int r = 0; r < RS; ++r) sm[WR::at(w, n0, ba, r)] = v[g + r * G];
+          for (int j = 0; j <= M; ++j) ad[j] = base + L::kW * (j ^ (b & M));
+#pragma unroll
+          for (int r = 0; r < RS; ++r) sm[ad[r & M] + L::kW * (r & ~M)] = v[g + r * G];
+        }
+      } else {
+        using WR = Strided<L, OPS, NS>;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int b = t + g * QR;
+          const int k = b & (NS - 1);
+          const int n0 = (b / NS) * NS * RS + k;
+          const int ba = WR::base(w, n0);
+#pragma unroll
+          for (int r = 0; r < RS; ++r) sm[WR::at(w, n0, ba, r)] = v[g + r * G];
+        }
       }
       Stages<Q, R, INV, L, COL, NS * RS, OPS>::run(v, sm, tw, t, w);
     }

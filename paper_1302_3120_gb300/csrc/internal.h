@@ -17,7 +17,7 @@ constexpr uint32_t kMinKey = 1u << 23;   // keys below this are 0 or subnormal |
 constexpr uint32_t kNoCandidates = 0xffffffffu;
 
 // Device-latched error bits (reported by csar_plan_check).
-enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u };
+enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
 
 // Column-pass modes.
 enum ColMode : int {

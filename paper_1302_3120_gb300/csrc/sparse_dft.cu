@@ -3,9 +3,10 @@
 // The first column pass of G(X) transforms X^(i), which has at most K nonzeros
 // (K = 20000 on 8192 x 8192: ~2.4 per column).  For a group of 16 columns holding
 // few entries, X[k, col] = sum_e x_e W_N^(k row_e) is cheaper than an N-point FFT:
-// one warp per column accumulates its entries for 8 output rows per lane (the
-// twiddle advances by W_N^(32 row_e) per row step from an exact table start), a
-// 256 x 16 block is staged in shared memory and written as 128-byte row segments.
+// the group's entries are bucketed by column in shared memory, one warp per column
+// accumulates its own entries for 8 output rows per lane (the twiddle advances by
+// W_N^(32 row_e) per row step from an exact table start), and a 256 x 16 block is
+// staged in shared memory and written as 128-byte row segments.
 // Groups with more entries are left to the FFT path (k_col, COL_SPARSE_FWD).
 #include "fft.cuh"
 #include "internal.h"
@@ -18,9 +19,10 @@ constexpr int kSdRows = kDirectRows;          // output rows per chunk (8 per la
 template <int N>
 __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_tile, int chunks_per_cta) {
   __shared__ float2 tw[kTwLo + kTwHi];
+  __shared__ uint32_t e_key[kDirectMaxEntries];   // flat index, then (column, row) order key
   __shared__ uint32_t e_row[kDirectMaxEntries];
   __shared__ float2 e_val[kDirectMaxEntries];
-  __shared__ int e_col[kDirectMaxEntries];
+  __shared__ int col_beg[kDirectCols + 1];
   __shared__ float2 blk[kSdRows][kDirectCols + 1];
   if (a.gate && *a.gate != a.gate_val) return;
   const int grp = blockIdx.x;
@@ -33,26 +35,41 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_ti
   const int tid = threadIdx.x;
   load_twiddles(tw, a.tw);
   const int col0 = grp * kDirectCols;
-  // entries in ascending flat index (list order comes from atomics): the sums below
-  // then have a fixed order and the pass is deterministic
+  // Entries ordered by (column, row): each warp then walks only its own column, and
+  // the order (hence the summation order) does not depend on the list order, which
+  // comes from atomics: the pass is deterministic.
+  uint32_t key = 0u;
+  float2 val = make_float2(0.f, 0.f);
   if (tid < ne) {
     const uint32_t idx = a.xs_idx[e0 + tid];
+    const uint32_t row = idx / (uint32_t)a.nr;
+    const uint32_t cl = idx % (uint32_t)a.nr - (uint32_t)col0;
+    key = (cl << 16) | row;                     // row < 2^13, column < 16
+    val = a.xs_val[e0 + tid];
+    e_key[tid] = key;
+  }
+  __syncthreads();
+  if (tid < ne) {
     int rank = 0;
-    for (int j = 0; j < ne; ++j) rank += a.xs_idx[e0 + j] < idx;
-    e_row[rank] = idx / (uint32_t)a.nr;
-    e_col[rank] = (int)(idx % (uint32_t)a.nr) - col0;
-    e_val[rank] = a.xs_val[e0 + tid];
+    for (int j = 0; j < ne; ++j) rank += e_key[j] < key;
+    e_row[rank] = key & 0xffffu;
+    e_val[rank] = val;
+  }
+  if (tid <= kDirectCols) {
+    int cnt = 0;
+    for (int j = 0; j < ne; ++j) cnt += (int)(e_key[j] >> 16) < tid;
+    col_beg[tid] = cnt;
   }
   __syncthreads();
   const int w = tid >> 5, lane = tid & 31;
+  const int i0 = col_beg[w], i1 = col_beg[w + 1];
   constexpr int kScale = kTwN / N;            // W_N^m = W_8192^(m * kScale)
   for (int ch = 0; ch < chunks_per_cta; ++ch) {
     const int k0 = (blockIdx.y * chunks_per_cta + ch) * kSdRows;
     float2 acc[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int i = 0; i < ne; ++i) {
-      if (e_col[i] != w) continue;            // uniform per warp
+    for (int i = i0; i < i1; ++i) {           // uniform per warp
       const uint32_t row = e_row[i];
       const float2 x = e_val[i];
       float2 e = cmul(x, twiddle_tab<false>(tw, (int)(((uint32_t)(k0 + lane) * row) % N) * kScale));

@@ -191,3 +191,23 @@ def test_dense_iterate_groups_are_deterministic():
     assert np.array_equal(a, b)
     x_ref, _ = ita.ita(g, y, mask, K, 8)
     assert metrics.rel_l2(a, x_ref) < 1e-3
+
+
+@pytest.mark.parametrize("na,nr,p", [(8192, 64, 1), (8192, 64, 2), (8192, 64, 4), (8192, 64, 8),
+                                     (8192, 64, 16), (4096, 128, 1), (4096, 128, 4),
+                                     (4096, 128, 8), (2048, 128, 2), (2048, 128, 4)])
+def test_every_column_cluster_size(na, nr, p):
+    """The column passes under every cluster size they are built for (cross-CTA
+    exchanges of the blocked and strided transforms, the residue pass, the selection
+    and the sparse-input FFT path): 3 NIHT iterations on a 2% scene against the
+    oracle."""
+    csar = lib()
+    g, xt, y, mask = _problem(31, na, nr, frac=0.02)
+    K = int(round(0.02 * na * nr))
+    x_ref, st_ref = ita.ita(g, y, mask, K, 3, mu_mode="niht")
+    plan = csar.csar_plan_create(g, flags=csar.plan_col_cluster(p))
+    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 3, mu_mode="niht", stats=True)
+    csar.csar_plan_check(plan)
+    assert metrics.rel_l2(host(X), x_ref) < 1e-3
+    sig_ref = np.array([s_.sigma for s_ in st_ref])
+    assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-4
