@@ -18,7 +18,8 @@
 // Modes (the fused work of one ITA iteration, Algorithm 1 / Eq. (25)):
 //   COL_FWD / COL_INV      plain azimuth FFT / IFFT (operators G and M)
 //   COL_SPARSE_FWD         the K-sparse iterate scattered into a zero tile, then FFT
-//   COL_RESID              IFFT -> G(X); r = S.(Y - G(X)); FFT -> input of M
+//   COL_RESID              IFFT -> G(X); mask S; FFT -> F_a(S.G(X)) (the next range
+//                          pass subtracts it from F_a(S.Y): F_a of the residue)
 //   COL_SELECT / REPASS    IFFT -> Delta X = M(r); Delta X at the support; histogram
 //                          of |Delta X|^2 keys and compaction of the candidates for
 //                          the (K+1)-th magnitude (Section IV-B)
@@ -209,10 +210,17 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
   float2* tw = smem + L::kSmemElems;
   float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);   // 32 floats
   uint64_t* mbar = reinterpret_cast<uint64_t*>(red + 32);      // kMbCount mbarriers
-  uint32_t* hist = reinterpret_cast<uint32_t*>(mbar + kMbCount);  // kHistBins (SELECT)
+  uint32_t* hist = reinterpret_cast<uint32_t*>(mbar + kMbCount);  // kHistBins (SELECT, REPASS)
+  uint32_t* msk = hist + kHistBins;                                // NT words (SELECT, REPASS)
 
+  uint32_t rstate = kRepassNone;
   if constexpr (MODE == COL_REPASS) {
-    if (a.ctl->need_repass == 0) return;   // uniform for the whole grid
+    // uniform for the whole grid: the first re-pass launch (gate_val kRepassCut) runs in
+    // states kRepassCut and kRepassHist, the second (kRepassCut2) in state kRepassCut2
+    rstate = a.ctl->need_repass;
+    const bool run = a.gate_val == kRepassCut2 ? rstate == kRepassCut2
+                                               : (rstate == kRepassCut || rstate == kRepassHist);
+    if (!run) return;
   }
   if (a.gate && *a.gate != a.gate_val) return;
   const int c = (P > 1) ? (int)(blockIdx.x % P) : 0;      // rank in the cluster
@@ -310,35 +318,17 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     for (int s = 0; s < R; ++s)
       __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], cscale(v[s], a.scale));
   } else if constexpr (MODE == COL_RESID) {
-    // F_a r = F_a(S.Y) - F_a(S.g): the transformed masked echo (a.y) is subtracted
-    // at the store, so only the mask bits stay live between the two transforms;
-    // ||r||^2 follows from Parseval, sum |F_a r|^2 / N_a.
+    // F_a(S.g): the residue F_a r = F_a(S.Y) - F_a(S.g) is formed by the next range pass
+    // as it loads its rows (contiguous reads there, where the pass hides their latency)
     bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
     for (int s = 0; s < R; ++s)
       v[s] = ((mbits >> s) & 1u) ? cscale(v[s], a.scale) : make_float2(0.f, 0.f);
     fft<Q, false, L, true, R>(v, sm, tw, t, w);
-    float acc = 0.f;
-    bool bad = false;
-    // The values of F_a(S.Y) are loaded in groups before any of them is used, so their
-    // latencies overlap (a load between two stores would wait for the previous store).
     if constexpr (P == 1) {
-      constexpr int kG = R / 4;
 #pragma unroll
-      for (int g0 = 0; g0 < R; g0 += kG) {
-        float2 yv[kG];
-#pragma unroll
-        for (int s = 0; s < kG; ++s) yv[s] = __ldcs(&a.y[(size_t)(t + (g0 + s) * QR) * nr + col]);
-#pragma unroll
-        for (int s = 0; s < kG; ++s) {
-          const size_t idx = (size_t)(t + (g0 + s) * QR) * nr + col;
-          const float2 r = csub(yv[s], v[g0 + s]);
-          bad |= !(isfinite(r.x) && isfinite(r.y));
-          acc += cabs2(r);
-          __stcs(&a.out[idx], r);
-        }
-      }
+      for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)(t + s * QR) * nr + col], v[s]);
     } else {
       // SB step: twiddle W_N^(c k2) (k2 = t + s QR) and push k2 to CTA s / RP at element
       // c*Q/P + k2l (source-major, so pushes and the final reads are conflict-free), once
@@ -362,46 +352,20 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
         }
       }
       xch_signal<P>(mb0 + 8u * kMbSb);
-      // v is dead here: its registers receive this thread's values of F_a(S.Y) (in two
-      // groups), so the loads of the first group overlap the wait
-      constexpr int kGI = C::RP >= 2 ? C::RP / 2 : 1;   // i-values per group
-      const float2* yc = a.y + (size_t)(c * (Q / P) + t) * nr + col;
+      mbar_wait(mb0 + 8u * kMbSb, 0u, a.ctl);
       float2* oc = a.out + (size_t)(c * (Q / P) + t) * nr + col;
       const size_t di = (size_t)QR * nr, dk = (size_t)Q * nr;
-      float2 yv[kGI * P];
 #pragma unroll
-      for (int i = 0; i < kGI; ++i)
+      for (int i = 0; i < C::RP; ++i) {
+        const int k2l = t + QR * i;
+        float2 b[P];
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) yv[i * P + k1] = __ldcs(yc + i * di + k1 * dk);
-      mbar_wait(mb0 + 8u * kMbSb, 0u, a.ctl);
+        for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, n1 * (Q / P) + k2l)];
+        Dft<P, false>::run(b);
 #pragma unroll
-      for (int i0 = 0; i0 < C::RP; i0 += kGI) {
-        if (i0 > 0) {
-#pragma unroll
-          for (int i = 0; i < kGI; ++i)
-#pragma unroll
-            for (int k1 = 0; k1 < P; ++k1) yv[i * P + k1] = __ldcs(yc + (i0 + i) * di + k1 * dk);
-        }
-#pragma unroll
-        for (int i = 0; i < kGI; ++i) {
-          const int k2l = t + QR * (i0 + i);
-          float2 b[P];
-#pragma unroll
-          for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, n1 * (Q / P) + k2l)];
-          Dft<P, false>::run(b);
-#pragma unroll
-          for (int k1 = 0; k1 < P; ++k1) {
-            const float2 r = csub(yv[i * P + k1], b[k1]);
-            bad |= !(isfinite(r.x) && isfinite(r.y));
-            acc += cabs2(r);
-            __stcs(oc + (i0 + i) * di + k1 * dk, r);
-          }
-        }
+        for (int k1 = 0; k1 < P; ++k1) __stcs(oc + i * di + k1 * dk, b[k1]);
       }
     }
-    if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
-    const float tot = block_sum<NT>(acc, red);
-    if (tid == 0) a.partial[blockIdx.x] = tot * a.scale;
   } else if constexpr (MODE == COL_NORM) {
     bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
@@ -411,41 +375,50 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     const float tot = block_sum<NT>(acc, red);
     if (tid == 0) a.partial[blockIdx.x] = tot;
   } else {  // COL_SELECT / COL_REPASS
-    constexpr bool HIST = (MODE == COL_SELECT);
-    if constexpr (HIST) {
+    // COL_SELECT: histogram of off-support keys >= hist_floor(cut), candidates >= cut,
+    // Delta X at the support.  COL_REPASS: full histogram and no candidates in state
+    // kRepassHist, candidates only otherwise.
+    const bool hist_on = (MODE == COL_SELECT) || rstate == kRepassHist;
+    const uint32_t floor_key = (MODE == COL_SELECT) ? hist_floor(sel_cut) : 0u;
+    const uint32_t cut = (MODE == COL_REPASS && rstate == kRepassHist) ? kNoCandidates : sel_cut;
+    if (hist_on) {
       for (int i = tid; i < (int)kHistBins; i += NT) hist[i] = 0u;
     }
+    msk[tid] = 0u;
     bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
     __syncthreads();
-    // local element m of this CTA is global row c + P*m
-#pragma unroll
-    for (int s = 0; s < R; ++s) sm[L::template at<4>(w, t + s * QR)] = cscale(v[s], a.scale);
-    __syncthreads();
-    // support of the current iterate: record Delta X there, exclude from candidates
+    // support of the current iterate: local element m (global row c + P*m) of column w
+    // is v[m / QR] of thread (m % QR)*W + w, which gets bit m / QR in its support word
+    const uint32_t first_idx = sel_idx;
     for (uint32_t e = sel_e0 + tid; e < sel_e1; e += NT) {
       const uint32_t idx = sel_idx;
       if (e + NT < sel_e1) sel_idx = a.xs_idx[e + NT];
       const int row = (int)(idx / (uint32_t)a.nr);
       if (P > 1 && row % P != c) continue;
       const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
-      const int p = L::template at<4>(ww, row / P);
-      if constexpr (HIST) a.xs_dx[e] = sm[p];
-      sm[p] = make_float2(__int_as_float(0x7fffffff), 0.f);
+      const int m = row / P;
+      atomicOr(&msk[(m % QR) * W + ww], 1u << (m / QR));
     }
     __syncthreads();
-    const uint32_t cut = sel_cut;
+    const uint32_t sup = msk[tid];
+    if constexpr (MODE == COL_SELECT) {
+      // Delta X at the support goes through shared memory to the entry's thread
+      if (sup) {
+#pragma unroll
+        for (int s = 0; s < R; ++s)
+          if ((sup >> s) & 1u) sm[L::template at<4>(w, t + s * QR)] = cscale(v[s], a.scale);
+      }
+    }
     constexpr uint32_t full = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
     const int lane = tid & 31;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
       const int m = t + s * QR;
-      const float2 d = sm[L::template at<4>(w, m)];
-      const bool on_support = isnan(d.x);
+      const float2 d = cscale(v[s], a.scale);
+      const bool on_support = (sup >> s) & 1u;
       const uint32_t key = __float_as_uint(cabs2(d)) & 0x7fffffffu;
-      if constexpr (HIST) {
-        if (!on_support) atomicAdd(&hist[key >> kHistShift], 1u);
-      }
+      if (hist_on && !on_support && key >= floor_key) atomicAdd(&hist[key >> kHistShift], 1u);
       const bool take = !on_support && key >= cut && key >= kMinKey;
       const uint32_t bal = __ballot_sync(full, take);
       if (bal) {
@@ -462,8 +435,17 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
         }
       }
     }
-    if constexpr (HIST) {
-      __syncthreads();
+    if (MODE == COL_SELECT || hist_on) __syncthreads();
+    if constexpr (MODE == COL_SELECT) {
+      for (uint32_t e = sel_e0 + tid; e < sel_e1; e += NT) {
+        const uint32_t idx = e == sel_e0 + tid ? first_idx : a.xs_idx[e];
+        const int row = (int)(idx / (uint32_t)a.nr);
+        if (P > 1 && row % P != c) continue;
+        const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
+        a.xs_dx[e] = sm[L::template at<4>(ww, row / P)];
+      }
+    }
+    if (hist_on) {
       for (int i = tid; i < (int)kHistBins; i += NT) {
         const uint32_t h = hist[i];
         if (h) atomicAdd(&a.hist[i], h);
@@ -471,7 +453,8 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     }
   }
   // no CTA may exit while a peer could still address its shared memory: every remote
-  // store above is followed by a cluster barrier, so none is outstanding here
+  // store or arrive into this CTA precedes a completed wait of this CTA on an exchange
+  // mbarrier, so none is outstanding here
 }
 
 // Sampling mask in the residual pass's register order: word ((col*P + c)*QR + t) holds
@@ -502,7 +485,7 @@ static size_t col_smem(int mode) {
   using L = Layout<C::Q, C::W, true>;
   size_t b = (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
              32 * sizeof(float) + kMbCount * sizeof(uint64_t);
-  if (mode == COL_SELECT) b += kHistBins * sizeof(uint32_t);
+  if (mode == COL_SELECT || mode == COL_REPASS) b += (kHistBins + C::NT) * sizeof(uint32_t);
   return b;
 }
 

@@ -257,6 +257,7 @@ struct csar_plan_s {
   float2* tw = nullptr;
   Buffers b;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cond_stream = nullptr;   // captures the bodies of conditional graph nodes
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   GraphKey key[2];
   bool use_graphs = true;
@@ -388,6 +389,7 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   s.xo_idx = b.idx[nxt];
   s.xo_val = b.val[nxt];
   s.partial = b.partial;
+  s.n_partial_resid = row_ctas(plan->na, plan->nr);
   s.partial_norm = b.partial_norm;
   s.n_partial = plan->n_tiles * plan->col_p;
   s.stats = b.stats;
@@ -407,6 +409,48 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
     cudaError_t e_ = (call);              \
     if (e_ != cudaSuccess) return e_;     \
   } while (0)
+
+// True while `s` is being captured into a graph.
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+
+// A conditional handle of the graph being captured on `s` (reset to 0 at every launch).
+cudaError_t capture_handle(cudaStream_t s, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  LK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  return cudaGraphConditionalHandleCreate(h, g, 0u, cudaGraphCondAssignDefault);
+}
+
+// While capturing `s`: append an IF node on handle `h` whose body is what `body`
+// enqueues (captured through `aux`), so work that is rarely needed costs no launch when
+// a kernel upstream leaves the handle at 0.  Not capturing: `body` runs on `s` directly
+// (its kernels then test the same condition on the device and return early).
+template <class F>
+cudaError_t enqueue_if(cudaStream_t s, cudaStream_t aux, cudaGraphConditionalHandle h, F&& body) {
+  if (!h) return body(s);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  LK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  LK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  LK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  LK(cudaStreamBeginCaptureToGraph(aux, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  const cudaError_t e = body(aux);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(aux, &out);
+  return e != cudaSuccess ? e : e2;
+}
 
 // One ITA iteration reading the sparse iterate in list `cur` and writing list 1-cur.
 // Optional per-pass events (profiling): ev[0..kPasses].
@@ -430,23 +474,43 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(mark(1));
   LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
   LK(mark(2));
-  // residue r = S.(Y - G(X)), produced directly as F_a r = F_a(S.Y) - F_a(S.G(X))
+  // residue r = S.(Y - G(X)), produced as F_a r = F_a(S.Y) - F_a(S.G(X)): this column
+  // pass forms F_a(S.G(X)), the next range pass subtracts it from F_a(S.Y)
   c.in = b.z;
   c.out = b.z;
-  c.y = b.yf;
   (void)y;
   c.mask = mask;
   LK(launch_col(na, plan->col_p, COL_RESID, c, nt, s));
   LK(mark(3));
-  // M(r): range pass with H1, H2, H3
-  LK(launch_row(nr, row_args(plan, b.z, plan->coef_m), s));
+  // M(r): range pass with H1, H2, H3 on F_a r = F_a(S.Y) - F_a(S.G(X))
+  RowArgs rm = row_args(plan, b.z, plan->coef_m);
+  rm.yf = b.yf;
+  rm.partial = b.partial;
+  rm.ctl = b.ctl;
+  rm.resid_scale = 1.0f / (float)na;
+  LK(launch_row(nr, rm, s));
   LK(mark(4));
   // Delta X = F_a^-1: support values, histogram, candidates
   LK(launch_col(na, plan->col_p, COL_SELECT, c, nt, s));
   LK(mark(5));
   SelArgs sa = sel_args(plan, cur, o);
+  // the re-passes are conditional graph nodes when captured (set by the check kernels)
+  if (capturing(s)) {
+    LK(capture_handle(s, &sa.h_repass));
+    LK(capture_handle(s, &sa.h_repass2));
+  }
   LK(launch_sel_check(sa, s));
-  LK(launch_col(na, plan->col_p, COL_REPASS, c, nt, s));
+  LK(enqueue_if(s, plan->cond_stream, sa.h_repass, [&](cudaStream_t q) {
+    ColArgs r = c;
+    r.gate_val = kRepassCut;
+    return launch_col(na, plan->col_p, COL_REPASS, r, nt, q);
+  }));
+  LK(enqueue_if(s, plan->cond_stream, sa.h_repass2, [&](cudaStream_t q) {
+    LK(launch_sel_check2(sa, q));
+    ColArgs r = c;
+    r.gate_val = kRepassCut2;
+    return launch_col(na, plan->col_p, COL_REPASS, r, nt, q);
+  }));
   if (o.mu_mode == CSAR_MU_NIHT) {
     // NIHT step on Gamma = supp X^(i) (skipped on the device when the support is empty)
     ColArgs g = col_args(plan);
@@ -776,7 +840,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(dalloc(&b.hist2, kHistBins));
   PK(dalloc(&b.tile_cnt, nt));
   PK(dalloc(&b.tile_cur, nt));
-  PK(dalloc(&b.partial, (size_t)nt * plan->col_p));
+  PK(dalloc(&b.partial, (size_t)std::max(nt * plan->col_p, row_ctas(plan->na, plan->nr))));
   PK(dalloc(&b.partial_norm, (size_t)nt * plan->col_p));
   PK(dalloc(&b.mask_t, (size_t)col_mask_words(plan->na, plan->nr, plan->col_p)));
   PK(dalloc(&b.ctl, 1));
@@ -785,6 +849,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(cudaMemset(b.tile_cnt, 0, nt * sizeof(uint32_t)));
   PK(cudaMemset(b.ctl, 0, sizeof(Ctl)));
   PK(cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking));
+  PK(cudaStreamCreateWithFlags(&plan->cond_stream, cudaStreamNonBlocking));
 #undef PK
   *out = plan;
   return CSAR_OK;
@@ -796,6 +861,7 @@ csar_status csar_plan_destroy(csar_plan plan) {
   cudaDeviceSynchronize();
   drop_graphs(plan);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  if (plan->cond_stream) cudaStreamDestroy(plan->cond_stream);
   free_buffers(plan->b);
   if (plan->coef_g) cudaFree(plan->coef_g);
   if (plan->coef_m) cudaFree(plan->coef_m);

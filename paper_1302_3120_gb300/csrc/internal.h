@@ -15,6 +15,21 @@ constexpr uint32_t kHistBins = 4096;     // column-pass histogram: key >> 19 (bi
 constexpr int kHistShift = 19;
 constexpr uint32_t kMinKey = 1u << 23;   // keys below this are 0 or subnormal |b|^2
 constexpr uint32_t kNoCandidates = 0xffffffffu;
+// The selection column pass histograms only keys at or above a floor 16 bins (two
+// octaves of |Delta X|^2) under the bin of the candidate cut; with no cut yet (the
+// first iteration) the floor is 0 and the histogram is complete.
+constexpr uint32_t kFloorBins = 16;
+__host__ __device__ constexpr uint32_t hist_floor(uint32_t cut) {
+  return cut == kNoCandidates ? 0u
+         : ((cut >> kHistShift) > kFloorBins ? (((cut >> kHistShift) - kFloorBins) << kHistShift) : 0u);
+}
+// Re-pass states (Ctl::need_repass), set by the check kernels.
+enum : uint32_t {
+  kRepassNone = 0,   // the candidates of the selection pass are complete
+  kRepassCut = 1,    // re-pass with the exact cut (first re-pass)
+  kRepassHist = 2,   // the (K+1)-th key lies under the floor: full-histogram re-pass first
+  kRepassCut2 = 3,   // then the exact cut from that histogram (second re-pass)
+};
 
 // Device-latched error bits (reported by csar_plan_check).
 enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
@@ -24,9 +39,11 @@ enum ColMode : int {
   COL_FWD = 0,        // out = F_a in
   COL_INV = 1,        // out = F_a^-1 in
   COL_SPARSE_FWD = 2, // out = F_a (list scattered into a zero tile)
-  COL_RESID = 3,      // g = F_a^-1 in; out = F_a(S.Y) - F_a(S.g) = F_a r; partial ||r||^2
+  COL_RESID = 3,      // g = F_a^-1 in; out = F_a(S.g) (the range pass forms F_a r)
   COL_SELECT = 4,     // dx = F_a^-1 in; Delta X at the support; histogram; candidates
-  COL_REPASS = 5,     // COL_SELECT again with the exact cut, only if ctl->need_repass
+  COL_REPASS = 5,     // re-pass of COL_SELECT: gate_val 1 runs in states kRepassCut
+                      // (candidates) and kRepassHist (full histogram), gate_val 3 in
+                      // state kRepassCut2 (candidates)
   COL_NORM = 6,       // g = F_a^-1 in; partial sum of S.|g|^2 (no store)
 };
 
@@ -102,6 +119,14 @@ struct RowArgs {
   uint32_t gate_val;
   int n_rows;
   float scale;              // 1/N_r of the range IFFT
+  // residue form (range pass of M in the ITA): if yf is non-null the pass transforms
+  // yf - data (F_a(S.Y) - F_a(S.G X) = F_a r), writes one partial sum of |F_a r|^2 *
+  // resid_scale per CTA into partial[blockIdx.x] (||r||^2 by Parseval with 1/N_a) and
+  // latches kErrNonfinite in ctl->err for non-finite values
+  const float2* yf;
+  float* partial;
+  Ctl* ctl;
+  float resid_scale;
 };
 
 // Column passes: a cluster of P CTAs owns col_w(N, P) adjacent columns; each CTA
@@ -121,6 +146,7 @@ __host__ __device__ constexpr long long col_mask_words(int na, int nr, int p) {
 }
 __host__ __device__ constexpr int row_w(int n) { return n >= 8192 ? 1 : 8192 / n; }
 __host__ __device__ constexpr int row_threads(int n) { return n * row_w(n) / regs_for(n); }
+__host__ __device__ constexpr int row_ctas(int na, int nr) { return (na + row_w(nr) - 1) / row_w(nr); }
 
 // Direct DFT of the K-sparse iterate (k_sparse_dft): groups of kDirectCols columns
 // holding at most kDirectMaxEntries entries skip the FFT.
@@ -163,7 +189,8 @@ struct SelArgs {
   uint32_t* xo_off;           // next iterate (bucketed)
   uint32_t* xo_idx;
   float2* xo_val;
-  const float* partial;       // residual partials of the column pass (COL_RESID)
+  const float* partial;       // residual partials of the range pass of M (one per CTA)
+  int n_partial_resid;
   const float* partial_norm;  // NIHT denominator partials (COL_NORM)
   int n_partial;
   IterStat* stats;
@@ -175,9 +202,14 @@ struct SelArgs {
   int thresh;                 // 0 soft, 1 half
   int mu_mode;                // 0 fixed, 1 NIHT
   float mu_fixed;
+  // conditional graph nodes of the re-passes (0 when not captured): sel_check sets
+  // h_repass in states kRepassCut / kRepassHist and h_repass2 in state kRepassHist
+  cudaGraphConditionalHandle h_repass;
+  cudaGraphConditionalHandle h_repass2;
 };
 
 cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_sel_check2(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_sel_round(const SelArgs& a, int level, cudaStream_t s);
 cudaError_t launch_sel_pick(const SelArgs& a, int level, cudaStream_t s);
 cudaError_t launch_thr_count(const SelArgs& a, cudaStream_t s);

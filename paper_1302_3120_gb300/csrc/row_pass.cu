@@ -8,6 +8,9 @@
 //
 // With (pro, mid, epi) = (H1, H2, H3) this is the middle of the focusing operator M;
 // with the conjugates (H3*, H2*, H1*) it is the middle of G (Section III-C/D).
+// In the ITA's range pass of M the pass first forms its input F_a r = F_a(S.Y) -
+// F_a(S.G(X)) from the echo's azimuth transform and the residue column pass's output,
+// with the partial sums of |F_a r|^2.
 // j' = j - N_r/2 is the signed range-time bin, m the signed range-frequency bin;
 // each phase is evaluated on the fly from per-row FP64-derived coefficients
 // (phase.cuh), so the pass reads and writes each element exactly once.
@@ -36,6 +39,38 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   float2 v[R];
 #pragma unroll
   for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+  if (a.yf) {
+    // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
+    const float2* yp = a.yf + (size_t)(live ? row : 0) * N;
+    float acc = 0.f;
+    bool bad = false;
+    constexpr int kG = R >= 8 ? 8 : R;   // loads in flight per group (register pressure)
+#pragma unroll
+    for (int g0 = 0; g0 < R; g0 += kG) {
+      float2 y[kG];
+#pragma unroll
+      for (int j = 0; j < kG; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kG; ++j) {
+        v[g0 + j] = csub(y[j], v[g0 + j]);
+        acc += cabs2(v[g0 + j]);
+        bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
+      }
+    }
+    if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);
+    constexpr int kWarps = row_threads(N) / 32;
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      float tot = 0.f;
+#pragma unroll
+      for (int i = 0; i < kWarps; ++i) tot += red[i];
+      a.partial[blockIdx.x] = tot * a.resid_scale;
+    }
+  }
   {
     const PhaseCoef c = cp->pro;
     phase_ap<R, 0, R>(v, c, t - N / 2, QR, 1.f, phase_second_diff(c, QR));
@@ -62,7 +97,8 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
 template <int N>
 static size_t row_smem() {
   using L = Layout<N, row_w(N), false>;
-  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2);
+  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
+         32 * sizeof(float);
 }
 
 #define CSAR_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)

@@ -8,7 +8,10 @@
 //
 //   sel_check   finds the histogram bin holding the (K+1)-th largest off-support
 //               |Delta X|^2; if the cut was above that bin's lower edge (or the
-//               candidate buffer overflowed) it asks for one exact re-pass.
+//               candidate buffer overflowed) it asks for one exact re-pass.  The
+//               column pass counts only keys at or above a floor under the cut; if
+//               the (K+1)-th key lies below it, a full-histogram re-pass and a
+//               second check (sel_check2) come first.
 //   sel_round/  three rounds of radix select (12 + 12 + 8 key bits) over the union
 //   sel_pick    {support} u {candidates} give the exact key of |b|_(K+1)^2.
 //   thr_count/  strict |b| > sigma entries are counted per column tile, scanned,
@@ -107,32 +110,69 @@ __device__ int find_bin(const uint32_t* h, int nb, uint64_t target, uint64_t* ab
 }
 
 // ------------------------------------------------------------------ check / repass
+// Capacity check of a re-pass with cut bin lb: off-support keys at or above it.
+__device__ void check_capacity(const SelArgs& a, int lb) {
+  unsigned long long cnt = 0;
+  for (int i = lb; i < (int)kHistBins; ++i) cnt += a.hist[i];
+  if (cnt > a.cand_cap) atomicOr(&a.ctl->err, kErrCapacity);
+}
+
 __global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
   __shared__ unsigned long long sh[kSelThreads];
+  __shared__ uint32_t state;
   Ctl* c = a.ctl;
   const uint64_t target = (uint64_t)a.K + 1;
   uint64_t above = 0;
   const int b = find_bin(a.hist, kHistBins, target, &above, sh);
   if (threadIdx.x == 0) {
-    uint32_t low = b > 0 ? ((uint32_t)b << kHistShift) : 0u;
-    if (low < kMinKey) low = kMinKey;
-    const bool ok = c->cut_key <= low && c->cand_count <= a.cand_cap;
-    c->need_repass = ok ? 0u : 1u;
-    if (!ok) {
-      c->cut_key = low;
+    // the selection pass counted only keys >= hist_floor(cut): if fewer than K+1 lie
+    // there, the (K+1)-th off-support key is below the floor and its bin is unknown
+    const bool truncated = hist_floor(c->cut_key) > 0u;
+    if (b < 0 && truncated) {
+      c->need_repass = kRepassHist;
+      c->cut_key = kNoCandidates;
       c->cand_count = 0u;
+    } else {
+      uint32_t low = b > 0 ? ((uint32_t)b << kHistShift) : 0u;
+      if (low < kMinKey) low = kMinKey;
+      const bool ok = c->cut_key <= low && c->cand_count <= a.cand_cap;
+      c->need_repass = ok ? kRepassNone : kRepassCut;
+      if (!ok) {
+        c->cut_key = low;
+        c->cand_count = 0u;
+      }
     }
     // NIHT with an empty support (first iteration): select on Delta X (mu = 1),
     // then the step is computed on that top-K support and applied afterwards
     c->niht_first = (a.mu_mode == 1 && c->nx == 0u) ? 1u : 0u;
     if (a.mu_mode == 0 || c->nx == 0u) c->mu = a.mu_mode == 0 ? a.mu_fixed : 1.f;
+    state = c->need_repass;
+    if (a.h_repass && (state == kRepassCut || state == kRepassHist)) cudaGraphSetConditional(a.h_repass, 1u);
+    if (a.h_repass2 && state == kRepassHist) cudaGraphSetConditional(a.h_repass2, 1u);
   }
-  // capacity check of the re-pass: off-support keys >= the new cut
-  if (threadIdx.x == 0 && c->need_repass) {
-    const int lb = b > 0 ? b : (int)(kMinKey >> kHistShift);
-    unsigned long long cnt = 0;
-    for (int i = lb; i < (int)kHistBins; ++i) cnt += a.hist[i];
-    if (cnt > a.cand_cap) atomicOr(&c->err, kErrCapacity);
+  __syncthreads();
+  if (state == kRepassHist) {
+    // the full-histogram re-pass counts into a cleared histogram
+    for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x) a.hist_mut[i] = 0u;
+  } else if (state == kRepassCut && threadIdx.x == 0) {
+    check_capacity(a, b > 0 ? b : (int)(kMinKey >> kHistShift));
+  }
+}
+
+// After a full-histogram re-pass: the exact cut, and the second (candidate) re-pass.
+__global__ void __launch_bounds__(kSelThreads) k_sel_check2(SelArgs a) {
+  __shared__ unsigned long long sh[kSelThreads];
+  Ctl* c = a.ctl;
+  if (c->need_repass != kRepassHist) return;   // uniform
+  uint64_t above = 0;
+  const int b = find_bin(a.hist, kHistBins, (uint64_t)a.K + 1, &above, sh);
+  if (threadIdx.x == 0) {
+    uint32_t low = b > 0 ? ((uint32_t)b << kHistShift) : 0u;
+    if (low < kMinKey) low = kMinKey;
+    c->cut_key = low;
+    c->cand_count = 0u;
+    c->need_repass = kRepassCut2;
+    check_capacity(a, b > 0 ? b : (int)(kMinKey >> kHistShift));
   }
 }
 
@@ -311,7 +351,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
   Ctl* c = a.ctl;
   const int tid = threadIdx.x;
   double r = 0.0;
-  for (int i = tid; i < a.n_partial; i += kSelThreads) r += (double)a.partial[i];
+  for (int i = tid; i < a.n_partial_resid; i += kSelThreads) r += (double)a.partial[i];
   sd[tid] = r;
   __syncthreads();
   for (int off = kSelThreads / 2; off > 0; off >>= 1) {
@@ -433,6 +473,10 @@ static int grid_ctas() {
 
 cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s) {
   k_sel_check<<<1, kSelThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_sel_check2(const SelArgs& a, cudaStream_t s) {
+  k_sel_check2<<<1, kSelThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_sel_round(const SelArgs& a, int level, cudaStream_t s) {

@@ -211,3 +211,31 @@ def test_every_column_cluster_size(na, nr, p):
     assert metrics.rel_l2(host(X), x_ref) < 1e-3
     sig_ref = np.array([s_.sigma for s_ in st_ref])
     assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-4
+
+
+@pytest.mark.parametrize("rate,iters", [(0.8, 4), (0.95, 3)])
+def test_sharp_threshold_drops(rate, iters):
+    """Noiseless bright sparse scene at high sampling: sigma falls by 4x (0.8) or 13x
+    (0.95) per iteration, so the candidate cut predicted from the previous sigma is too
+    high (exact re-pass) or the (K+1)-th key lies under the histogram floor (full
+    re-pass, second check, candidate re-pass).  The GPU follows the oracle."""
+    csar = lib()
+    na = nr = 256
+    g = synth.airborne(na, nr)
+    rng = np.random.default_rng(3)
+    k = 60 if rate > 0.9 else 30
+    x = np.zeros((na, nr), complex)
+    idx = rng.choice(na * nr, k, replace=False)
+    x.flat[idx] = 10 * np.exp(2j * np.pi * rng.random(k))
+    mask = synth.bernoulli_mask(rng, na, nr, rate)
+    y = mask * csa.observe_G(g, x)
+    x_ref, st_ref = ita.ita(g, y, mask, k, iters)
+    sig_ref = np.array([s_.sigma for s_ in st_ref])
+    assert np.max(sig_ref[:-1] / sig_ref[1:]) > (6.0 if rate > 0.9 else 3.0)
+    plan = csar.csar_plan_create(g)
+    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), k, iters, stats=True)
+    csar.csar_plan_check(plan)
+    assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-2
+    xg = host(X)
+    assert set(np.flatnonzero(xg)) == set(np.flatnonzero(x_ref))
+    assert metrics.rel_l2(xg, x_ref) < 1e-3
