@@ -79,8 +79,11 @@ typedef struct csar_plan_s* csar_plan;
 typedef struct csar_batch_s* csar_batch;
 
 /* csar_plan_create flags: force the column-pass cluster size (CTAs per column tile,
- * 1..16, power of two; 0 = the autotuned or default choice). */
+ * 1..16, power of two; 0 = the autotuned or default choice), and/or column-pass CTAs
+ * of 4096 complex values (four per SM, half-width tiles) instead of 8192 (two per SM).
+ * A configuration that is not built for n_az gives CSAR_E_UNSUPPORTED. */
 #define CSAR_PLAN_COL_CLUSTER(p) ((uint32_t)(p) << 8)
+#define CSAR_PLAN_COL_HALF_TILE ((uint32_t)1 << 16)
 
 enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };
 enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1 };
@@ -105,7 +108,8 @@ typedef struct {
 /* Create a plan: validates `params`, builds the FP64 phase-coefficient tables of
  * the chirp-scaling functions H1 (chirp scaling), H2 (range compression, SRC and
  * bulk RCMC) and H3 (azimuth matched filter and residual phase) and uploads them,
- * and allocates the plan's device workspace.  `flags` must be 0.  The plan uses the
+ * and allocates the plan's device workspace.  `flags`: 0 (the autotuned or default
+ * column configuration) or the CSAR_PLAN_COL_* flags above.  The plan uses the
  * current CUDA device.  On error *out is set to NULL.  CSAR_E_UNSUPPORTED if the
  * geometry's phase arguments exceed what the on-the-fly phase evaluation covers
  * (|range-linear term| >= 2^22 cycles). */
@@ -228,9 +232,11 @@ csar_status csar_solve_batched(csar_batch batch, const void* const* Y_dev,
 csar_status csar_batch_check(csar_batch batch);
 
 /* Autotuner: times `iters` ITA iterations on synthetic data for every column-pass
- * cluster size available for (n_az, n_rg), keeps the fastest for plans created
+ * configuration available for (n_az, n_rg), keeps the fastest for plans created
  * afterwards in this process (and in the file named by CSAR_TUNE_FILE, if set), and
- * returns it in *chosen_cluster.  Synchronises the device; allocates temporaries. */
+ * returns it in *chosen_cluster.  Both CTA sizes (CSAR_PLAN_COL_HALF_TILE or not) are
+ * tried; *chosen_cluster reports the cluster size of the chosen configuration.
+ * Synchronises the device; allocates temporaries. */
 csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster);
 
 /* Synchronise the plan's device and report (and clear) any latched device-side

@@ -434,7 +434,8 @@ def csar_batch_check(batch: Batch) -> None:
 
 
 def csar_autotune(geometry, iters: int = 10) -> int:
-    """Time every column-pass cluster size for this shape; later plans use the fastest."""
+    """Time every column-pass configuration for this shape; later plans use the fastest.
+    Returns the cluster size of the chosen configuration."""
     p = params_of(geometry)
     out = ctypes.c_int32(0)
     _check(lib.csar_autotune(ctypes.byref(p), int(iters), ctypes.byref(out)), "csar_autotune")
@@ -444,3 +445,7 @@ def csar_autotune(geometry, iters: int = 10) -> int:
 def plan_col_cluster(p: int) -> int:
     """csar_plan_create flag forcing the column-pass cluster size."""
     return int(p) << 8
+
+
+# csar_plan_create flag: column-pass CTAs of 4096 complex values (half-width tiles)
+PLAN_COL_HALF_TILE = 1 << 16

@@ -56,11 +56,12 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   }
 }
 
-template <int N, int P_>
+template <int N, int P_, int E_ = kColCtaElems>
 struct ColCfg {
   static constexpr int P = P_;
+  static constexpr int E = E_;
   static constexpr int Q = N / P;
-  static constexpr int W = col_w(N, P);
+  static constexpr int W = col_w(N, P, E);
   static constexpr int R = col_regs(Q);
   static constexpr int QR = Q / R;
   static constexpr int NT = QR * W;
@@ -144,11 +145,11 @@ enum : int { kMbBs = 0, kMbFree = 1, kMbSb = 2, kMbCount = 4 };
 // pushed to element n2 of CTA k1.  Then the canonical input of the local FFT is read.
 // The twiddles W_N^(n2 k1) are W^(n2 k1) = w1^k1 (w1 = W^n2 from the table) within
 // each group of four k1, re-anchored from the table at every multiple of four.
-template <int N, int P, bool INV>
-__device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* sm, const float2* tw,
+template <int N, int P, int E, bool INV>
+__device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P, E>::R], float2* sm, const float2* tw,
                                          int c, int t, int w, const uint32_t (&peer)[P],
                                          uint32_t mb, Ctl* ctl) {
-  using C = ColCfg<N, P>;
+  using C = ColCfg<N, P, E>;
   using L = Layout<C::Q, C::W, true>;
   if constexpr (C::P > 1) {
 #pragma unroll
@@ -181,9 +182,9 @@ __device__ __forceinline__ void bs_cross(float2 (&v)[ColCfg<N, P>::R], float2* s
 }
 
 // Global row of v-slot s before the cross step (blocked input) for CTA c.
-template <int N, int P>
+template <int N, int P, int E>
 __device__ __forceinline__ int bs_in_row(int c, int t, int s) {
-  using C = ColCfg<N, P>;
+  using C = ColCfg<N, P, E>;
   if constexpr (C::P == 1) {
     return t + s * C::QR;
   } else {
@@ -193,16 +194,16 @@ __device__ __forceinline__ int bs_in_row(int c, int t, int s) {
 }
 
 // Global row of canonical slot s after the local FFT (strided output) for CTA c.
-template <int N, int P>
+template <int N, int P, int E>
 __device__ __forceinline__ int strided_row(int c, int t, int s) {
-  using C = ColCfg<N, P>;
+  using C = ColCfg<N, P, E>;
   return c + C::P * (t + s * C::QR);
 }
 
-template <int N, int P, int MODE>
-__global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs a) {
-  static_assert(ColCfg<N, P>::NT <= 1024, "block too large");
-  using C = ColCfg<N, P>;
+template <int N, int P, int E, int MODE>
+__global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col(ColArgs a) {
+  static_assert(ColCfg<N, P, E>::NT <= 1024, "block too large");
+  using C = ColCfg<N, P, E>;
   constexpr int W = C::W, R = C::R, QR = C::QR, NT = C::NT, Q = C::Q;
   using L = Layout<Q, W, true>;
   extern __shared__ float2 smem[];
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     }
   } else {
 #pragma unroll
-    for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P>(c, t, s) * nr + col]);
+    for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P, E>(c, t, s) * nr + col]);
   }
   // selection passes: the support range of this tile, its first entry per thread and the
   // candidate cut are fetched while the column loads are in flight
@@ -307,20 +308,20 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
 
   // ------------------------------------------------------------------ transforms
   if constexpr (MODE == COL_FWD || MODE == COL_SPARSE_FWD) {
-    bs_cross<N, P, false>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
+    bs_cross<N, P, E, false>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, false, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
-    for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], v[s]);
+    for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)strided_row<N, P, E>(c, t, s) * nr + col], v[s]);
   } else if constexpr (MODE == COL_INV) {
-    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
+    bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
     for (int s = 0; s < R; ++s)
-      __stcs(&a.out[(size_t)strided_row<N, P>(c, t, s) * nr + col], cscale(v[s], a.scale));
+      __stcs(&a.out[(size_t)strided_row<N, P, E>(c, t, s) * nr + col], cscale(v[s], a.scale));
   } else if constexpr (MODE == COL_RESID) {
     // F_a(S.g): the residue F_a r = F_a(S.Y) - F_a(S.g) is formed by the next range pass
     // as it loads its rows (contiguous reads there, where the pass hides their latency)
-    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
+    bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
     for (int s = 0; s < R; ++s)
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
       }
     }
   } else if constexpr (MODE == COL_NORM) {
-    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
+    bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
     float acc = 0.f;
 #pragma unroll
@@ -381,11 +382,17 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
     const bool hist_on = (MODE == COL_SELECT) || rstate == kRepassHist;
     const uint32_t floor_key = (MODE == COL_SELECT) ? hist_floor(sel_cut) : 0u;
     const uint32_t cut = (MODE == COL_REPASS && rstate == kRepassHist) ? kNoCandidates : sel_cut;
+    // histogram bins: all kHistBins without a floor, else a window of kHistWindow bins
+    // from the floor's bin whose last bin also takes every larger key (so the global
+    // bin found for the (K+1)-th key is still a valid lower bound)
+    const int hb0 = (int)(floor_key >> kHistShift);
+    const int nbins = floor_key == 0u ? (int)kHistBins
+                                      : ((int)kHistBins - hb0 < kHistWindow ? (int)kHistBins - hb0 : kHistWindow);
     if (hist_on) {
-      for (int i = tid; i < (int)kHistBins; i += NT) hist[i] = 0u;
+      for (int i = tid; i < nbins; i += NT) hist[i] = 0u;
     }
     msk[tid] = 0u;
-    bs_cross<N, P, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
+    bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
     __syncthreads();
     // support of the current iterate: local element m (global row c + P*m) of column w
@@ -418,7 +425,10 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
       const float2 d = cscale(v[s], a.scale);
       const bool on_support = (sup >> s) & 1u;
       const uint32_t key = __float_as_uint(cabs2(d)) & 0x7fffffffu;
-      if (hist_on && !on_support && key >= floor_key) atomicAdd(&hist[key >> kHistShift], 1u);
+      if (hist_on && !on_support && key >= floor_key) {
+        const int hb = (int)(key >> kHistShift) - hb0;
+        atomicAdd(&hist[hb < nbins ? hb : nbins - 1], 1u);
+      }
       const bool take = !on_support && key >= cut && key >= kMinKey;
       const uint32_t bal = __ballot_sync(full, take);
       if (bal) {
@@ -446,9 +456,9 @@ __global__ void __launch_bounds__(ColCfg<N, P>::NT, kColCtasPerSm) k_col(ColArgs
       }
     }
     if (hist_on) {
-      for (int i = tid; i < (int)kHistBins; i += NT) {
+      for (int i = tid; i < nbins; i += NT) {
         const uint32_t h = hist[i];
-        if (h) atomicAdd(&a.hist[i], h);
+        if (h) atomicAdd(&a.hist[hb0 + i], h);
       }
     }
   }
@@ -479,9 +489,9 @@ __global__ void k_mask_transpose(const uint32_t* __restrict__ mask, uint32_t* __
   }
 }
 
-template <int N, int P>
+template <int N, int P, int E>
 static size_t col_smem(int mode) {
-  using C = ColCfg<N, P>;
+  using C = ColCfg<N, P, E>;
   using L = Layout<C::Q, C::W, true>;
   size_t b = (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
              32 * sizeof(float) + kMbCount * sizeof(uint64_t);
@@ -489,13 +499,13 @@ static size_t col_smem(int mode) {
   return b;
 }
 
-template <int N, int P, int MODE>
+template <int N, int P, int E, int MODE>
 static cudaError_t col_launch_mode(const ColArgs& a, int n_tiles, cudaStream_t s) {
-  using C = ColCfg<N, P>;
+  using C = ColCfg<N, P, E>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_tiles * C::P);
   cfg.blockDim = dim3(C::NT);
-  cfg.dynamicSmemBytes = col_smem<N, P>(MODE);
+  cfg.dynamicSmemBytes = col_smem<N, P, E>(MODE);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -504,18 +514,18 @@ static cudaError_t col_launch_mode(const ColArgs& a, int n_tiles, cudaStream_t s
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_col<N, P, MODE>, a);
+  return cudaLaunchKernelEx(&cfg, k_col<N, P, E, MODE>, a);
 }
 
-template <int N, int P>
+template <int N, int P, int E>
 static cudaError_t col_attrs() {
   cudaError_t e = cudaSuccess;
-#define CSAR_ATTR(M)                                                                        \
-  if (e == cudaSuccess)                                                                     \
-    e = cudaFuncSetAttribute(k_col<N, P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                             (int)col_smem<N, P>(M));                                       \
-  if (e == cudaSuccess && P > 8)                                                            \
-    e = cudaFuncSetAttribute(k_col<N, P, M>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+#define CSAR_ATTR(M)                                                                          \
+  if (e == cudaSuccess)                                                                       \
+    e = cudaFuncSetAttribute(k_col<N, P, E, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             (int)col_smem<N, P, E>(M));                                      \
+  if (e == cudaSuccess && P > 8)                                                              \
+    e = cudaFuncSetAttribute(k_col<N, P, E, M>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   CSAR_ATTR(COL_FWD)
   CSAR_ATTR(COL_INV)
   CSAR_ATTR(COL_SPARSE_FWD)
@@ -527,16 +537,16 @@ static cudaError_t col_attrs() {
   return e;
 }
 
-template <int N, int P>
+template <int N, int P, int E>
 static cudaError_t col_launch(ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s) {
   switch (mode) {
-    case COL_FWD: return col_launch_mode<N, P, COL_FWD>(a, n_tiles, s);
-    case COL_INV: return col_launch_mode<N, P, COL_INV>(a, n_tiles, s);
-    case COL_SPARSE_FWD: return col_launch_mode<N, P, COL_SPARSE_FWD>(a, n_tiles, s);
-    case COL_RESID: return col_launch_mode<N, P, COL_RESID>(a, n_tiles, s);
-    case COL_SELECT: return col_launch_mode<N, P, COL_SELECT>(a, n_tiles, s);
-    case COL_REPASS: return col_launch_mode<N, P, COL_REPASS>(a, n_tiles, s);
-    case COL_NORM: return col_launch_mode<N, P, COL_NORM>(a, n_tiles, s);
+    case COL_FWD: return col_launch_mode<N, P, E, COL_FWD>(a, n_tiles, s);
+    case COL_INV: return col_launch_mode<N, P, E, COL_INV>(a, n_tiles, s);
+    case COL_SPARSE_FWD: return col_launch_mode<N, P, E, COL_SPARSE_FWD>(a, n_tiles, s);
+    case COL_RESID: return col_launch_mode<N, P, E, COL_RESID>(a, n_tiles, s);
+    case COL_SELECT: return col_launch_mode<N, P, E, COL_SELECT>(a, n_tiles, s);
+    case COL_REPASS: return col_launch_mode<N, P, E, COL_REPASS>(a, n_tiles, s);
+    case COL_NORM: return col_launch_mode<N, P, E, COL_NORM>(a, n_tiles, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -547,14 +557,16 @@ static cudaError_t mask_transpose(int nr, const uint32_t* mask, uint32_t* mask_t
   return cudaGetLastError();
 }
 
-// Entry points of one (N, P) instantiation, used by the dispatcher in col_dispatch.cu.
-#define CSAR_COL_INSTANTIATE(N, P)                                                          \
-  cudaError_t col_attrs_##N##_##P() { return col_attrs<N, P>(); }                           \
-  cudaError_t col_launch_##N##_##P(ColMode m, const ColArgs& a, int nt, cudaStream_t s) {   \
-    return col_launch<N, P>(m, a, nt, s);                                                   \
-  }                                                                                         \
-  cudaError_t col_mask_##N##_##P(int nr, const uint32_t* mk, uint32_t* mt, cudaStream_t s) { \
-    return mask_transpose<N, P>(nr, mk, mt, s);                                             \
+// Entry points of one (N, P, E) instantiation, used by the dispatcher in col_dispatch.cu.
+// The column-order sampling mask depends on (N, P) only.
+#define CSAR_COL_INSTANTIATE(N, P, E)                                                              \
+  cudaError_t col_attrs_##N##_##P##_##E() { return col_attrs<N, P, E>(); }                         \
+  cudaError_t col_launch_##N##_##P##_##E(ColMode m, const ColArgs& a, int nt, cudaStream_t s) {    \
+    return col_launch<N, P, E>(m, a, nt, s);                                                       \
+  }
+#define CSAR_COL_MASK_INSTANTIATE(N, P)                                                            \
+  cudaError_t col_mask_##N##_##P(int nr, const uint32_t* mk, uint32_t* mt, cudaStream_t s) {       \
+    return mask_transpose<N, P>(nr, mk, mt, s);                                                    \
   }
 
 }  // namespace csar

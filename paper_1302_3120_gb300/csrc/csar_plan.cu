@@ -213,7 +213,7 @@ csar_status set_error(csar_status st, const char* msg) { return fail(st, "%s", m
 // afterwards in this process (optionally persisted in the file named by CSAR_TUNE_FILE).
 namespace {
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tune;
+std::map<std::pair<int, int>, std::pair<ColConf, ColConf>> g_tune;   // (main, residue)
 bool g_tune_loaded = false;
 
 void tune_load_locked() {
@@ -223,9 +223,16 @@ void tune_load_locked() {
   if (!f) return;
   FILE* fp = std::fopen(f, "r");
   if (!fp) return;
-  int na, nr, p;
-  while (std::fscanf(fp, "%d %d %d", &na, &nr, &p) == 3)
-    if (col_cluster_ok(na, p)) g_tune[{na, nr}] = p;
+  int na, nr, p, e, pr, er;
+  while (std::fscanf(fp, "%d %d %d %d %d %d", &na, &nr, &p, &e, &pr, &er) == 6) {
+    ColConf c, r;
+    c.p = p;
+    c.e = e;
+    r.p = pr;
+    r.e = er;
+    if (col_conf_ok(na, c) && col_conf_ok(na, r) && col_w(na, p, e) == col_w(na, pr, er))
+      g_tune[{na, nr}] = {c, r};
+  }
   std::fclose(fp);
 }
 
@@ -234,15 +241,20 @@ void tune_save_locked() {
   if (!f) return;
   FILE* fp = std::fopen(f, "w");
   if (!fp) return;
-  for (const auto& kv : g_tune) std::fprintf(fp, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+  for (const auto& kv : g_tune)
+    std::fprintf(fp, "%d %d %d %d %d %d\n", kv.first.first, kv.first.second, kv.second.first.p,
+                 kv.second.first.e, kv.second.second.p, kv.second.second.e);
   std::fclose(fp);
 }
 
-int tuned_cluster(int na, int nr) {
+bool tuned_conf(int na, int nr, ColConf* c, ColConf* r) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load_locked();
   auto it = g_tune.find({na, nr});
-  return it == g_tune.end() ? 0 : it->second;
+  if (it == g_tune.end()) return false;
+  *c = it->second.first;
+  *r = it->second.second;
+  return true;
 }
 }  // namespace
 
@@ -251,7 +263,9 @@ struct csar_plan_s {
   int dev = 0;
   int na = 0, nr = 0;
   int64_t n = 0;
-  int col_p = 1, col_tile = 0, n_tiles = 0;
+  ColConf col;                    // column-pass configuration (cluster size, values per CTA)
+  ColConf col_res;                // configuration of the residue and NIHT-norm passes (same W)
+  int col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
   float2* tw = nullptr;
@@ -391,7 +405,7 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   s.partial = b.partial;
   s.n_partial_resid = row_ctas(plan->na, plan->nr);
   s.partial_norm = b.partial_norm;
-  s.n_partial = plan->n_tiles * plan->col_p;
+  s.n_partial = plan->n_tiles * plan->col_res.p;
   s.stats = b.stats;
   s.K = o.K;
   s.n = plan->n;
@@ -470,7 +484,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   // G(X): F_a of the sparse iterate, range pass with conj(H3), conj(H2), conj(H1)
   c.out = b.z;
   LK(launch_sparse_dft(na, c, plan->col_tile, s));
-  LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, c, nt, s));
+  LK(launch_col(na, plan->col, COL_SPARSE_FWD, c, nt, s));
   LK(mark(1));
   LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
   LK(mark(2));
@@ -480,7 +494,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   c.out = b.z;
   (void)y;
   c.mask = mask;
-  LK(launch_col(na, plan->col_p, COL_RESID, c, nt, s));
+  LK(launch_col(na, plan->col_res, COL_RESID, c, nt, s));
   LK(mark(3));
   // M(r): range pass with H1, H2, H3 on F_a r = F_a(S.Y) - F_a(S.G(X))
   RowArgs rm = row_args(plan, b.z, plan->coef_m);
@@ -491,7 +505,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(launch_row(nr, rm, s));
   LK(mark(4));
   // Delta X = F_a^-1: support values, histogram, candidates
-  LK(launch_col(na, plan->col_p, COL_SELECT, c, nt, s));
+  LK(launch_col(na, plan->col, COL_SELECT, c, nt, s));
   LK(mark(5));
   SelArgs sa = sel_args(plan, cur, o);
   // the re-passes are conditional graph nodes when captured (set by the check kernels)
@@ -503,13 +517,13 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(enqueue_if(s, plan->cond_stream, sa.h_repass, [&](cudaStream_t q) {
     ColArgs r = c;
     r.gate_val = kRepassCut;
-    return launch_col(na, plan->col_p, COL_REPASS, r, nt, q);
+    return launch_col(na, plan->col, COL_REPASS, r, nt, q);
   }));
   LK(enqueue_if(s, plan->cond_stream, sa.h_repass2, [&](cudaStream_t q) {
     LK(launch_sel_check2(sa, q));
     ColArgs r = c;
     r.gate_val = kRepassCut2;
-    return launch_col(na, plan->col_p, COL_REPASS, r, nt, q);
+    return launch_col(na, plan->col, COL_REPASS, r, nt, q);
   }));
   if (o.mu_mode == CSAR_MU_NIHT) {
     // NIHT step on Gamma = supp X^(i) (skipped on the device when the support is empty)
@@ -521,7 +535,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_val = b.dx;
     g.out = b.z;
     LK(launch_sparse_dft(na, g, plan->col_tile, s));
-    LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
+    LK(launch_col(na, plan->col, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 0u;
@@ -529,7 +543,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
-    LK(launch_col(na, plan->col_p, COL_NORM, g, nt, s));
+    LK(launch_col(na, plan->col_res, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 0, s));
   }
   for (int lev = 0; lev < 3; ++lev) {
@@ -549,7 +563,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_val = b.val[nxt];
     g.out = b.z;
     LK(launch_sparse_dft(na, g, plan->col_tile, s));
-    LK(launch_col(na, plan->col_p, COL_SPARSE_FWD, g, nt, s));
+    LK(launch_col(na, plan->col, COL_SPARSE_FWD, g, nt, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 1u;
@@ -557,7 +571,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
-    LK(launch_col(na, plan->col_p, COL_NORM, g, nt, s));
+    LK(launch_col(na, plan->col_res, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 1, s));
   }
   if (b.ck_active)
@@ -607,10 +621,10 @@ cudaError_t dense_op(csar_plan plan, const float2* in, float2* out, bool is_g, c
   ColArgs c = col_args(plan);
   c.in = in;
   c.out = out;
-  LK(launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s));
+  LK(launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s));
   LK(launch_row(plan->nr, row_args(plan, out, is_g ? plan->coef_g : plan->coef_m), s));
   c.in = out;
-  return launch_col(plan->na, plan->col_p, COL_INV, c, plan->n_tiles, s);
+  return launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
 }
 
 csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* stream) {
@@ -626,10 +640,10 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
   ColArgs c = col_args(plan);
   c.in = (const float2*)in;
   c.out = (float2*)out;
-  cudaError_t e = launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s);
+  cudaError_t e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
   if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), s);
   c.in = (const float2*)out;
-  if (e == cudaSuccess) e = launch_col(plan->na, plan->col_p, COL_INV, c, plan->n_tiles, s);
+  if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
   if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G" : "csar_M");
   return CSAR_OK;
 }
@@ -638,12 +652,12 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
 // F_a(S . Y) (uses the pass-to-pass buffer as scratch).
 cudaError_t prepare_inputs(csar_plan plan, const float2* y, const uint32_t* mask, cudaStream_t s) {
   Buffers& b = plan->b;
-  LK(launch_mask_transpose(plan->na, plan->col_p, plan->nr, mask, b.mask_t, s));
+  LK(launch_mask_transpose(plan->na, plan->col_res.p, plan->nr, mask, b.mask_t, s));
   LK(launch_mask_apply(y, mask, b.z, plan->n, s));
   ColArgs c = col_args(plan);
   c.in = b.z;
   c.out = b.yf;
-  return launch_col(plan->na, plan->col_p, COL_FWD, c, plan->n_tiles, s);
+  return launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
 }
 
 csar_status latched(csar_plan plan) {
@@ -780,11 +794,18 @@ int32_t csar_version(void) { return 10000; }
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (flags & ~0xff00u) return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
+  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE))
+    return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
   const int forced_p = (int)((flags >> 8) & 0xffu);
-  if (forced_p && params && !col_cluster_ok(params->n_az, forced_p))
-    return fail(CSAR_E_UNSUPPORTED, "column cluster size %d not available for n_az=%d", forced_p,
-                params->n_az);
+  ColConf forced;
+  forced.p = forced_p;
+  forced.e = (flags & CSAR_PLAN_COL_HALF_TILE) ? kColCtaElems / 2 : kColCtaElems;
+  if ((forced_p || (flags & CSAR_PLAN_COL_HALF_TILE)) && params) {
+    if (!forced_p) forced.p = col_conf_default(params->n_az).p;
+    if (!col_conf_ok(params->n_az, forced))
+      return fail(CSAR_E_UNSUPPORTED, "column configuration (cluster %d, %d values per CTA) not available "
+                  "for n_az=%d", forced.p, forced.e, params->n_az);
+  }
   if (csar_status st = validate(params)) return st;
   std::vector<RowCoef> cg(params->n_az), cm(params->n_az);
   if (csar_status st = build_coefs_into(*params, cg.data(), cm.data())) return st;
@@ -796,9 +817,16 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->na = params->n_az;
   plan->nr = params->n_rg;
   plan->n = (int64_t)plan->na * plan->nr;
-  plan->col_p = forced_p ? forced_p : tuned_cluster(plan->na, plan->nr);
-  if (!plan->col_p) plan->col_p = col_cluster_default(plan->na);
-  plan->col_tile = col_w(plan->na, plan->col_p);
+  if (forced_p || (flags & CSAR_PLAN_COL_HALF_TILE)) {
+    plan->col = plan->col_res = forced;
+  } else if (!tuned_conf(plan->na, plan->nr, &plan->col, &plan->col_res)) {
+    plan->col = col_conf_default(plan->na);
+    plan->col_res = col_conf_default_res(plan->na);
+  }
+  // both configurations bucket the sparse iterate by the same tile width
+  if (col_w(plan->na, plan->col_res.p, plan->col_res.e) != col_w(plan->na, plan->col.p, plan->col.e))
+    plan->col_res = plan->col;
+  plan->col_tile = col_w(plan->na, plan->col.p, plan->col.e);
   plan->n_tiles = plan->nr / plan->col_tile;
   const char* ng = std::getenv("CSAR_NO_GRAPH");
   plan->use_graphs = !(ng && ng[0] == '1');
@@ -812,7 +840,8 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
     csar_status st_ = cuda_fail(e, #call);            \
     return bail(st_);                                 \
   }
-  PK(col_set_attributes(plan->na, plan->col_p));
+  PK(col_set_attributes(plan->na, plan->col));
+  PK(col_set_attributes(plan->na, plan->col_res));
   PK(row_set_attributes(plan->nr));
   PK(dalloc(&plan->coef_g, plan->na));
   PK(dalloc(&plan->coef_m, plan->na));
@@ -840,9 +869,9 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(dalloc(&b.hist2, kHistBins));
   PK(dalloc(&b.tile_cnt, nt));
   PK(dalloc(&b.tile_cur, nt));
-  PK(dalloc(&b.partial, (size_t)std::max(nt * plan->col_p, row_ctas(plan->na, plan->nr))));
-  PK(dalloc(&b.partial_norm, (size_t)nt * plan->col_p));
-  PK(dalloc(&b.mask_t, (size_t)col_mask_words(plan->na, plan->nr, plan->col_p)));
+  PK(dalloc(&b.partial, (size_t)std::max(nt * plan->col_res.p, row_ctas(plan->na, plan->nr))));
+  PK(dalloc(&b.partial_norm, (size_t)nt * plan->col_res.p));
+  PK(dalloc(&b.mask_t, (size_t)col_mask_words(plan->na, plan->nr, plan->col_res.p)));
   PK(dalloc(&b.ctl, 1));
   PK(cudaMemset(b.hist, 0, kHistBins * sizeof(uint32_t)));
   PK(cudaMemset(b.hist2, 0, kHistBins * sizeof(uint32_t)));
@@ -1193,41 +1222,55 @@ csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* cho
   o.mu_mode = CSAR_MU_FIXED;
   o.mu = 1.f;
   o.thresh = CSAR_THRESH_SOFT;
-  int best_p = 0;
-  float best_ms = 0.f;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  for (int p = 1; p <= 16; p <<= 1) {
-    if (!col_cluster_ok(na, p)) continue;
-    csar_plan plan = nullptr;
-    if (csar_plan_create(params, CSAR_PLAN_COL_CLUSTER(p), &plan) != CSAR_OK) continue;
-    float ms = -1.f;
-    if (csar_solve(plan, y, m, x, &o, nullptr, nullptr) == CSAR_OK) {   // warm-up and capture
-      cudaEventRecord(e0, 0);
-      const csar_status st = csar_solve(plan, y, m, x, &o, nullptr, nullptr);
-      cudaEventRecord(e1, 0);
-      if (st == CSAR_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-    }
-    csar_plan_destroy(plan);
-    if (ms > 0.f && (best_p == 0 || ms < best_ms)) {
-      best_p = p;
-      best_ms = ms;
+  // every configuration times the passes it serves (one profiled solve after a warm-up
+  // solve); per tile width the fastest for the main passes (sparse-input FFT, selection)
+  // and for the residue pass are combined, and the fastest width wins
+  struct Trial {
+    ColConf c;
+    int w;
+    float main_ms, res_ms;
+  };
+  std::vector<Trial> trials;
+  for (int half = 0; half < 2; ++half) {
+    for (int p = 1; p <= 16; p <<= 1) {
+      ColConf c;
+      c.p = p;
+      c.e = half ? kColCtaElems / 2 : kColCtaElems;
+      if (!col_conf_ok(na, c)) continue;
+      csar_plan plan = nullptr;
+      const uint32_t fl = CSAR_PLAN_COL_CLUSTER(p) | (half ? CSAR_PLAN_COL_HALF_TILE : 0u);
+      if (csar_plan_create(params, fl, &plan) != CSAR_OK) continue;
+      float pass[kPasses] = {};
+      const bool ok = csar_solve(plan, y, m, x, &o, nullptr, nullptr) == CSAR_OK &&
+                      csar_solve_profile(plan, y, m, x, &o, pass, kPasses, nullptr) == CSAR_OK;
+      csar_plan_destroy(plan);
+      if (ok) trials.push_back({c, col_w(na, c.p, c.e), pass[0] + pass[4] + pass[5], pass[2]});
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaFree(y);
   cudaFree(x);
   cudaFree(m);
-  if (!best_p) return fail(CSAR_E_INTERNAL, "autotune: no column configuration ran");
+  if (trials.empty()) return fail(CSAR_E_INTERNAL, "autotune: no column configuration ran");
+  ColConf best, best_res;
+  float best_ms = -1.f;
+  for (const Trial& a : trials) {
+    for (const Trial& r : trials) {
+      if (r.w != a.w) continue;
+      const float t = a.main_ms + r.res_ms;
+      if (best_ms < 0.f || t < best_ms) {
+        best_ms = t;
+        best = a.c;
+        best_res = r.c;
+      }
+    }
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load_locked();
-    g_tune[{na, nr}] = best_p;
+    g_tune[{na, nr}] = {best, best_res};
     tune_save_locked();
   }
-  if (chosen_cluster) *chosen_cluster = best_p;
+  if (chosen_cluster) *chosen_cluster = best.p;
   return CSAR_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr uint32_t kNoCandidates = 0xffffffffu;
 // octaves of |Delta X|^2) under the bin of the candidate cut; with no cut yet (the
 // first iteration) the floor is 0 and the histogram is complete.
 constexpr uint32_t kFloorBins = 16;
+constexpr int kHistWindow = 512;         // bins counted from the floor (64 octaves)
 __host__ __device__ constexpr uint32_t hist_floor(uint32_t cut) {
   return cut == kNoCandidates ? 0u
          : ((cut >> kHistShift) > kFloorBins ? (((cut >> kHistShift) - kFloorBins) << kHistShift) : 0u);
@@ -129,17 +130,19 @@ struct RowArgs {
   float resid_scale;
 };
 
-// Column passes: a cluster of P CTAs owns col_w(N, P) adjacent columns; each CTA
-// holds N*W/P <= 8192 complex64 values (64 KiB).  P is a plan choice among
-// col_cluster_ok(N, P) (see col_dispatch.cu).
-constexpr int kColCtaElems = 8192;   // complex64 values per column-pass CTA (64 KiB)
-constexpr int kColCtasPerSm = 2;
-__host__ __device__ constexpr int col_w(int n, int p) {
-  return (kColCtaElems / n) * p > 16 ? 16 : ((kColCtaElems / n) * p < 1 ? 1 : (kColCtaElems / n) * p);
+// Column passes: a cluster of P CTAs owns col_w(N, P, E) adjacent columns; each CTA
+// holds E = N*W/P complex64 values (E = 8192: 64 KiB and two CTAs per SM; E = 4096:
+// 32 KiB and four CTAs per SM).  A column configuration (P, E) is a plan choice among
+// col_conf_ok(N, conf) (see col_dispatch.cu).
+constexpr int kColCtaElems = 8192;   // default complex64 values per column-pass CTA
+struct ColConf {
+  int p = 1;                 // CTAs per cluster
+  int e = kColCtaElems;      // complex64 values per CTA
+};
+__host__ __device__ constexpr int col_w(int n, int p, int e = kColCtaElems) {
+  return e * p / n > 16 ? 16 : (e * p / n < 1 ? 1 : e * p / n);
 }
-__host__ __device__ constexpr int col_threads(int n, int p) {
-  return (n / p) / col_regs(n / p) * col_w(n, p);
-}
+__host__ __device__ constexpr int col_ctas_per_sm(int e) { return 2 * kColCtaElems / e; }
 // Words of the column-order sampling mask (one per thread and column of a pass).
 __host__ __device__ constexpr long long col_mask_words(int na, int nr, int p) {
   return (long long)nr * (na / col_regs(na / p));
@@ -161,14 +164,15 @@ void build_twiddles(float2* tw);
 csar_status set_error(csar_status st, const char* msg);
 
 // ---------------------------------------------------------------- launchers
-bool col_cluster_ok(int na, int p);
-int col_cluster_default(int na);
-cudaError_t launch_col(int na, int p, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
+bool col_conf_ok(int na, ColConf c);
+ColConf col_conf_default(int na);
+ColConf col_conf_default_res(int na);   // residue / NIHT-norm passes (same W as the default)
+cudaError_t launch_col(int na, ColConf conf, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);
 cudaError_t launch_mask_apply(const float2* y, const uint32_t* mask_bits, float2* out, long long n,
                               cudaStream_t s);
-cudaError_t col_set_attributes(int na, int p);
+cudaError_t col_set_attributes(int na, ColConf conf);
 cudaError_t launch_mask_transpose(int na, int p, int nr, const uint32_t* mask, uint32_t* mask_t,
                                   cudaStream_t s);
 cudaError_t row_set_attributes(int nr);

@@ -31,7 +31,7 @@ constexpr int kMaxDevices = 64;
 struct DeviceSetup {
   bool ready = false;
   unsigned char* ptr = nullptr;   // device address of g_noalloc_scratch on this device
-  bool col_done[14][5] = {};      // kernel attributes set for (log2 N_a, log2 P)
+  bool col_done[14][5][2] = {};   // kernel attributes set for (log2 N_a, log2 P, half tile)
   bool row_done[14] = {};         // ... and for log2 N_r
 };
 DeviceSetup g_setup[kMaxDevices];
@@ -77,10 +77,10 @@ extern "C" csar_status csar_G_noalloc(const csar_params* params, const void* x_d
     su.ptr = (unsigned char*)p;
     su.ready = true;
   }
-  const int p_col = col_cluster_default(na);
-  bool& cd = su.col_done[log2i(na)][log2i(p_col)];
+  const ColConf conf = col_conf_default(na);
+  bool& cd = su.col_done[log2i(na)][log2i(conf.p)][conf.e == kColCtaElems ? 0 : 1];
   if (!cd) {
-    if (col_set_attributes(na, p_col) != cudaSuccess)
+    if (col_set_attributes(na, conf) != cudaSuccess)
       return set_error(CSAR_E_CUDA, "csar_G_noalloc: column kernel attributes");
     cd = true;
   }
@@ -105,8 +105,8 @@ extern "C" csar_status csar_G_noalloc(const csar_params* params, const void* x_d
   c.in = (const float2*)x_dev;
   c.out = (float2*)y_dev;
   c.scale = 1.0f / (float)na;
-  const int n_tiles = nr / col_w(na, p_col);
-  if (e == cudaSuccess) e = launch_col(na, p_col, COL_FWD, c, n_tiles, s);
+  const int n_tiles = nr / col_w(na, conf.p, conf.e);
+  if (e == cudaSuccess) e = launch_col(na, conf, COL_FWD, c, n_tiles, s);
   RowArgs r{};
   r.data = (float2*)y_dev;
   r.coef = coef_d;
@@ -115,7 +115,7 @@ extern "C" csar_status csar_G_noalloc(const csar_params* params, const void* x_d
   r.scale = 1.0f / (float)nr;
   if (e == cudaSuccess) e = launch_row(nr, r, s);
   c.in = (const float2*)y_dev;
-  if (e == cudaSuccess) e = launch_col(na, p_col, COL_INV, c, n_tiles, s);
+  if (e == cudaSuccess) e = launch_col(na, conf, COL_INV, c, n_tiles, s);
   if (e != cudaSuccess) return set_error(CSAR_E_CUDA, cudaGetErrorString(e));
   return CSAR_OK;
 }

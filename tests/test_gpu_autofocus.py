@@ -42,7 +42,7 @@ def test_loss_and_direct_gradients(shape):
     assert metrics.rel_l2(gtd.cpu().numpy().astype(np.float64), gt) < 1e-4
 
 
-@pytest.mark.parametrize("shape,k,iters", [((64, 64), 40, 6), ((256, 256), 655, 10)])
+@pytest.mark.parametrize("shape,k,iters", [((64, 64), 40, 6), ((256, 256), 655, 10), ((2048, 128), 2621, 6)])
 def test_unrolled_gradient_matches_oracle(shape, k, iters):
     """dL/dtheta through the unrolled ITA: torch.autograd over the C-ABI forward and
     backward against the oracle's hand-derived adjoint (itself pinned by finite
@@ -67,7 +67,8 @@ def test_finite_differences_full_autofocus_workload():
     matches central differences of the GPU loss along random unit directions.  The
     unrolled loss is piecewise smooth (soft-threshold kinks at support changes) and its
     value carries fp32 rounding (~1e-4 relative at this residual level), so the step is
-    3e-3 rad and the bar 1e-2; the 1e-3 bar is checked against the FP64 oracle above."""
+    3e-3 rad and the bar 1e-2 of the derivative's typical size along a random unit
+    direction; the 1e-3 bar is checked against the FP64 oracle above."""
     import torch
     csar = lib()
     na = nr = 4096
@@ -88,7 +89,12 @@ def test_finite_differences_full_autofocus_workload():
     L.backward()
     grad = th.grad.double().cpu().numpy()
     eps = 3e-3
-    for _ in range(2):
+    # a random unit direction's derivative is typically |grad| / sqrt(n_az); one that is
+    # nearly orthogonal to grad has a much smaller derivative whose central difference is
+    # dominated by the loss's rounding, so the 1e-2 bar is relative to the larger of the
+    # two values and that typical size
+    typical = np.linalg.norm(grad) / np.sqrt(na)
+    for _ in range(3):
         d = rng.standard_normal(na)
         d /= np.linalg.norm(d)
         with torch.no_grad():
@@ -96,4 +102,4 @@ def test_finite_differences_full_autofocus_workload():
             lm = csar.autofocus_loss(plan, Y, md, _t(theta - eps * d), K, iters).item()
         fd = (lp - lm) / (2 * eps)
         an = float(np.dot(grad, d))
-        assert abs(fd - an) <= 1e-2 * max(abs(fd), abs(an)), (fd, an)
+        assert abs(fd - an) <= 1e-2 * max(abs(fd), abs(an), typical), (fd, an, typical)

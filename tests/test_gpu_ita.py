@@ -193,19 +193,23 @@ def test_dense_iterate_groups_are_deterministic():
     assert metrics.rel_l2(a, x_ref) < 1e-3
 
 
-@pytest.mark.parametrize("na,nr,p", [(8192, 64, 1), (8192, 64, 2), (8192, 64, 4), (8192, 64, 8),
-                                     (8192, 64, 16), (4096, 128, 1), (4096, 128, 4),
-                                     (4096, 128, 8), (2048, 128, 2), (2048, 128, 4)])
-def test_every_column_cluster_size(na, nr, p):
-    """The column passes under every cluster size they are built for (cross-CTA
-    exchanges of the blocked and strided transforms, the residue pass, the selection
-    and the sparse-input FFT path): 3 NIHT iterations on a 2% scene against the
-    oracle."""
+@pytest.mark.parametrize("na,nr,p,half", [
+    (8192, 64, 1, 0), (8192, 64, 2, 0), (8192, 64, 4, 0), (8192, 64, 8, 0), (8192, 64, 16, 0),
+    (8192, 64, 2, 1), (8192, 64, 4, 1), (8192, 64, 8, 1), (8192, 64, 16, 1),
+    (4096, 128, 1, 0), (4096, 128, 4, 0), (4096, 128, 8, 0), (4096, 128, 1, 1), (4096, 128, 2, 1),
+    (4096, 128, 4, 1), (4096, 128, 8, 1), (2048, 128, 2, 0), (2048, 128, 4, 0), (2048, 128, 1, 1), (2048, 128, 4, 1),
+    (1024, 128, 1, 1)])
+def test_every_column_configuration(na, nr, p, half):
+    """The column passes under every configuration they are built for (cluster size,
+    full or half tiles: cross-CTA exchanges of the blocked and strided transforms, the
+    residue pass, the selection and the sparse-input FFT path): 3 NIHT iterations on a
+    2% scene against the oracle."""
     csar = lib()
     g, xt, y, mask = _problem(31, na, nr, frac=0.02)
     K = int(round(0.02 * na * nr))
     x_ref, st_ref = ita.ita(g, y, mask, K, 3, mu_mode="niht")
-    plan = csar.csar_plan_create(g, flags=csar.plan_col_cluster(p))
+    flags = csar.plan_col_cluster(p) | (csar.PLAN_COL_HALF_TILE if half else 0)
+    plan = csar.csar_plan_create(g, flags=flags)
     X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 3, mu_mode="niht", stats=True)
     csar.csar_plan_check(plan)
     assert metrics.rel_l2(host(X), x_ref) < 1e-3
