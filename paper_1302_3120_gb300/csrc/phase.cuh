@@ -86,4 +86,41 @@ __device__ __forceinline__ void phase_ap(float2 (&v)[R], const PhaseCoef& c, int
   }
 }
 
+// Gamma[u] = exp(j 2 pi gamma u^2), gamma = C d^2: the quadratic part of phi along an
+// arithmetic progression of step d (d a power of two, so the scaling is exact).
+__device__ __forceinline__ float2 phase_gamma(const PhaseCoef& c, int d, int u) {
+  const float dd = (float)d * (float)d;
+  PhaseCoef g;
+  g.a_hi = g.a_lo = g.b_hi = g.b_lo = 0.f;
+  g.c_hi = c.c_hi * dd;
+  g.c_lo = c.c_lo * dd;
+  return phase_eval(g, u, 1.f);
+}
+
+// v[s] *= scale * exp(j 2 pi phi(i0 + (s - S0) d)) for s in [S0, S1), as one chain:
+//   phi(i0 + u d) = phi(i0) + u kappa + u^2 gamma,   kappa = d (B + 2 C i0),
+// so the factor is E Lambda^u Gamma[u] with E = exp(j 2 pi phi(i0)), Lambda =
+// exp(j 2 pi kappa) = exp(j 2 pi (phi(i0 + d) - phi(i0))) conj(Gamma[1]) and Gamma the
+// per-row table of phase_gamma.  Two exact evaluations per chain and three complex
+// products per element; the powers Lambda^u accumulate one rounding per step (a few
+// 1e-7 over 32 steps), the quadratic part comes exact from the table.
+template <int R, int S0, int S1>
+__device__ __forceinline__ void phase_chain(float2 (&v)[R], const PhaseCoef& c, int i0, int d,
+                                            float scale, const float2* gam) {
+  const float2 e0 = phase_eval(c, i0, 1.f);
+  const float2 e1 = phase_eval(c, i0 + d, 1.f);
+  const float2 q = make_float2(fmaf(e1.x, e0.x, e1.y * e0.y), fmaf(e1.y, e0.x, -e1.x * e0.y));  // e1 conj(e0)
+  const float2 g1 = gam[1];
+  const float2 lam = make_float2(fmaf(q.x, g1.x, q.y * g1.y), fmaf(q.y, g1.x, -q.x * g1.y));  // q conj(g1)
+  float2 p = make_float2(e0.x * scale, e0.y * scale);
+  v[S0] = cmul(v[S0], p);
+#pragma unroll
+  for (int s = S0 + 1; s < S1; ++s) v[s] = cmul(v[s], gam[s - S0]);
+#pragma unroll
+  for (int s = S0 + 1; s < S1; ++s) {
+    p = cmul(p, lam);
+    v[s] = cmul(v[s], p);
+  }
+}
+
 }  // namespace csar

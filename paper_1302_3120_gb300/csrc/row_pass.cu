@@ -19,6 +19,12 @@
 
 namespace csar {
 
+// Rows of at least 1024 bins apply each phase as chains along the thread's elements
+// (phase_chain, with per-row Gamma tables in shared memory); shorter rows, with many
+// rows per CTA, keep the re-anchored recurrence (phase_ap).
+template <int N>
+constexpr bool kRowChains = N >= 1024;
+
 template <int N>
 __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   constexpr int WR = row_w(N);
@@ -29,6 +35,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   if (a.gate && *a.gate != a.gate_val) return;
   float2* sm = smem;
   float2* tw = smem + L::kSmemElems;
+  float2* gam = tw + kTwLo + kTwHi + 16;   // after 32 floats of reduction scratch
   load_twiddles(tw, a.tw);
   const int tid = threadIdx.x;
   const int w = tid / QR, t = tid % QR;
@@ -39,6 +46,17 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   float2 v[R];
 #pragma unroll
   for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+  if constexpr (kRowChains<N>) {
+    // Gamma tables of this CTA's rows for the three phases: gam[(row*3 + phase)*R + u]
+    for (int i = tid; i < WR * 3 * R; i += row_threads(N)) {
+      const int rw = blockIdx.x * WR + i / (3 * R);
+      const RowCoef& rc = a.coef[rw < a.n_rows ? rw : 0];
+      const int ph = (i / R) % 3;
+      gam[i] = phase_gamma(ph == 0 ? rc.pro : (ph == 1 ? rc.mid : rc.epi), QR, i % R);
+    }
+    __syncthreads();
+  }
+  const float2* gw = gam + w * 3 * R;
   if (a.yf) {
     // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
     const float2* yp = a.yf + (size_t)(live ? row : 0) * N;
@@ -71,20 +89,27 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
       a.partial[blockIdx.x] = tot * a.resid_scale;
     }
   }
-  {
+  if constexpr (kRowChains<N>) {
+    phase_chain<R, 0, R>(v, cp->pro, t - N / 2, QR, 1.f, gw);
+  } else {
     const PhaseCoef c = cp->pro;
     phase_ap<R, 0, R>(v, c, t - N / 2, QR, 1.f, phase_second_diff(c, QR));
   }
   fft<N, false, L, false>(v, sm, tw, t, w);
-  {
-    // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
+  // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
+  if constexpr (kRowChains<N>) {
+    phase_chain<R, 0, R / 2>(v, cp->mid, t, QR, 1.f, gw + R);
+    phase_chain<R, R / 2, R>(v, cp->mid, t - (R / 2) * QR, QR, 1.f, gw + R);
+  } else {
     const PhaseCoef c = cp->mid;
     const float2 dd = phase_second_diff(c, QR);
     phase_ap<R, 0, R / 2>(v, c, t, QR, 1.f, dd);
     phase_ap<R, R / 2, R>(v, c, t - (R / 2) * QR, QR, 1.f, dd);
   }
   fft<N, true, L, false>(v, sm, tw, t, w);
-  {
+  if constexpr (kRowChains<N>) {
+    phase_chain<R, 0, R>(v, cp->epi, t - N / 2, QR, a.scale, gw + 2 * R);
+  } else {
     const PhaseCoef c = cp->epi;
     phase_ap<R, 0, R>(v, c, t - N / 2, QR, a.scale, phase_second_diff(c, QR));
   }
@@ -98,7 +123,7 @@ template <int N>
 static size_t row_smem() {
   using L = Layout<N, row_w(N), false>;
   return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
-         32 * sizeof(float);
+         32 * sizeof(float) + (kRowChains<N> ? (size_t)row_w(N) * 3 * regs_for(N) * sizeof(float2) : 0);
 }
 
 #define CSAR_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
