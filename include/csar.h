@@ -239,8 +239,16 @@ csar_status csar_batch_check(csar_batch batch);
  * Synchronises the device; allocates temporaries. */
 csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster);
 
+/* Self-test of failure detection: runs the bounded wait of the column-pass cluster
+ * exchanges on an mbarrier that nothing arrives at, with a limit of limit_ms (1..10000)
+ * milliseconds, on the current device (legacy stream; synchronises).  Returns
+ * CSAR_E_TIMEOUT when the wait ran out and the kernel returned normally (the expected
+ * outcome; the context stays usable), CSAR_E_INTERNAL if the wait completed.  The paper
+ * has no counterpart: it checks that no device-side wait of the library can hang. */
+csar_status csar_selftest_wait_timeout(int32_t limit_ms);
+
 /* Synchronise the plan's device and report (and clear) any latched device-side
- * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, ...). */
+ * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, CSAR_E_TIMEOUT, ...). */
 csar_status csar_plan_check(csar_plan plan);
 
 /* Thread-local description of the last error on this thread ("" if none). */

@@ -55,7 +55,7 @@ EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_it
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
            "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
-           "csar_batch_check", "csar_autotune")
+           "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout")
 
 
 def _load() -> ctypes.CDLL:
@@ -84,6 +84,7 @@ def _load() -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(Opts), vp]
     lib.csar_batch_check.argtypes = [vp]
     lib.csar_autotune.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(i32)]
+    lib.csar_selftest_wait_timeout.argtypes = [i32]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
@@ -431,6 +432,12 @@ def csar_solve_batched(batch: Batch, Ys, masks, Ks, iters: int, mu_mode="fixed",
 
 def csar_batch_check(batch: Batch) -> None:
     _check(lib.csar_batch_check(batch.handle), "csar_batch_check")
+
+
+def csar_selftest_wait_timeout(limit_ms: int = 20) -> int:
+    """Run the column-pass exchange wait on an mbarrier nothing arrives at; returns the
+    status (CSAR_E_TIMEOUT = 5 is the expected outcome)."""
+    return int(lib.csar_selftest_wait_timeout(int(limit_ms)))
 
 
 def csar_autotune(geometry, iters: int = 10) -> int:

@@ -114,19 +114,21 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of the local mbarrier at `a`, for one second at most: a peer
-// that never signals makes the kernel latch kErrTimeout and go on (no endless spin).
-__device__ __forceinline__ void mbar_wait(uint32_t a, uint32_t parity, Ctl* ctl) {
-  if (mbar_test(a, parity)) return;
+// Wait for phase `parity` of the local mbarrier at `a`, for limit_ns at most; false if
+// the limit ran out (no endless spin).
+__device__ __forceinline__ bool mbar_wait_for(uint32_t a, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_test(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     for (int k = 0; k < 64; ++k)
-      if (mbar_test(a, parity)) return;
-    if (global_ns() - t0 > 1000000000ull) {
-      if (ctl) atomicOr(&ctl->err, kErrTimeout);
-      return;
-    }
+      if (mbar_test(a, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
+}
+// The exchange waits of the column passes: one second at most, after which a peer that
+// never signalled makes the kernel latch kErrTimeout and go on.
+__device__ __forceinline__ void mbar_wait(uint32_t a, uint32_t parity, Ctl* ctl) {
+  if (!mbar_wait_for(a, parity, 1000000000ull) && ctl) atomicOr(&ctl->err, kErrTimeout);
 }
 // Signal on mbarrier `mb` (local address; the same offset in every CTA) of all P CTAs
 // that this CTA's prior shared-memory work (remote stores, or reads of its own buffer)
