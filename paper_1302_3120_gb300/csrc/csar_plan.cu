@@ -265,6 +265,7 @@ struct csar_plan_s {
   int64_t n = 0;
   ColConf col;                    // column-pass configuration (cluster size, values per CTA)
   ColConf col_res;                // configuration of the residue and NIHT-norm passes (same W)
+  int sel_fused_ok = 1;           // one-CTA selection allowed (CSAR_SEL_FUSED=0 disables it)
   int col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
@@ -415,6 +416,7 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   s.thresh = o.thresh;
   s.mu_mode = o.mu_mode;
   s.mu_fixed = o.mu;
+  s.fused_ok = plan->sel_fused_ok;
   return s;
 }
 
@@ -509,9 +511,14 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(mark(5));
   SelArgs sa = sel_args(plan, cur, o);
   // the re-passes are conditional graph nodes when captured (set by the check kernels)
-  if (capturing(s)) {
+  const bool cap = capturing(s);
+  if (cap) {
     LK(capture_handle(s, &sa.h_repass));
     LK(capture_handle(s, &sa.h_repass2));
+    if (o.mu_mode == CSAR_MU_FIXED) {
+      LK(capture_handle(s, &sa.h_fused));
+      LK(capture_handle(s, &sa.h_multi));
+    }
   }
   LK(launch_sel_check(sa, s));
   LK(enqueue_if(s, plan->cond_stream, sa.h_repass, [&](cudaStream_t q) {
@@ -546,13 +553,24 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     LK(launch_col(na, plan->col_res, COL_NORM, g, nt, s));
     LK(launch_niht_mu_mode(sa, 0, s));
   }
-  for (int lev = 0; lev < 3; ++lev) {
-    LK(launch_sel_round(sa, lev, s));
-    LK(launch_sel_pick(sa, lev, s));
+  // selection and threshold: one CTA when the union fits (fixed step), else the
+  // grid-wide radix select; the check kernel decides (conditional nodes when captured,
+  // early exits otherwise)
+  auto multi = [&](cudaStream_t q) -> cudaError_t {
+    for (int lev = 0; lev < 3; ++lev) {
+      LK(launch_sel_round(sa, lev, q));
+      LK(launch_sel_pick(sa, lev, q));
+    }
+    LK(launch_thr_count(sa, q));
+    LK(launch_thr_scan(sa, q));
+    return launch_thr_scatter_mode(sa, o.mu_mode == CSAR_MU_NIHT ? 1 : 0, q);
+  };
+  if (o.mu_mode == CSAR_MU_FIXED) {
+    LK(enqueue_if(s, plan->cond_stream, sa.h_fused, [&](cudaStream_t q) { return launch_sel_fused(sa, q); }));
+    LK(enqueue_if(s, plan->cond_stream, sa.h_multi, multi));
+  } else {
+    LK(multi(s));
   }
-  LK(launch_thr_count(sa, s));
-  LK(launch_thr_scan(sa, s));
-  LK(launch_thr_scatter_mode(sa, o.mu_mode == CSAR_MU_NIHT ? 1 : 0, s));
   if (o.mu_mode == CSAR_MU_NIHT) {
     // first iteration: Gamma = the top-K list just written (raw Delta X values)
     ColArgs g = col_args(plan);
@@ -828,6 +846,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
     plan->col_res = plan->col;
   plan->col_tile = col_w(plan->na, plan->col.p, plan->col.e);
   plan->n_tiles = plan->nr / plan->col_tile;
+  if (const char* sf = std::getenv("CSAR_SEL_FUSED")) plan->sel_fused_ok = sf[0] != '0';
   const char* ng = std::getenv("CSAR_NO_GRAPH");
   plan->use_graphs = !(ng && ng[0] == '1');
   auto bail = [&](csar_status st) {
@@ -840,6 +859,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
     csar_status st_ = cuda_fail(e, #call);            \
     return bail(st_);                                 \
   }
+  PK(sel_set_attributes());
   PK(col_set_attributes(plan->na, plan->col));
   PK(col_set_attributes(plan->na, plan->col_res));
   PK(row_set_attributes(plan->nr));

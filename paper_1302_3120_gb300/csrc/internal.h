@@ -69,7 +69,14 @@ struct Ctl {
   float2 b_jstar;        // b at jstar
   double niht_num;       // ||Delta X_Gamma||^2
   double niht_den;       // ||S . G(Delta X_Gamma)||^2
+  uint32_t sel_fused;    // 1: this iteration's selection runs in the one-CTA kernel
+  uint32_t pad2;
 };
+
+// One-CTA selection (k_sel_fused): used when the union of support and candidates fits
+// in its shared memory and the step is fixed.
+constexpr int kFusedMaxUnion = 40960;
+constexpr int kFusedMaxTiles = 4096;
 
 // Per-iteration checkpoint of the ITA unroll (autofocus backward).
 struct CkptMeta {
@@ -210,6 +217,10 @@ struct SelArgs {
   // h_repass in states kRepassCut / kRepassHist and h_repass2 in state kRepassHist
   cudaGraphConditionalHandle h_repass;
   cudaGraphConditionalHandle h_repass2;
+  // selection path (0 when not captured): sel_check sets exactly one of them
+  cudaGraphConditionalHandle h_fused;
+  cudaGraphConditionalHandle h_multi;
+  int fused_ok;               // 0: always the grid-wide path (CSAR_SEL_FUSED=0)
 };
 
 cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s);
@@ -223,6 +234,8 @@ cudaError_t launch_thr_scatter_mode(const SelArgs& a, int raw, cudaStream_t s);
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s);
+cudaError_t sel_set_attributes();
 
 // autofocus (autofocus.cu)
 cudaError_t launch_rotate_rows(const float2* y, const float* theta, float2* yt, int na, int nr,

@@ -149,6 +149,12 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
     state = c->need_repass;
     if (a.h_repass && (state == kRepassCut || state == kRepassHist)) cudaGraphSetConditional(a.h_repass, 1u);
     if (a.h_repass2 && state == kRepassHist) cudaGraphSetConditional(a.h_repass2, 1u);
+    // the one-CTA selection when no re-pass changes the union and it fits
+    const bool fused = a.fused_ok && a.mu_mode == 0 && state == kRepassNone &&
+                       union_size(c, a.cand_cap) <= (uint32_t)kFusedMaxUnion && a.n_tiles <= kFusedMaxTiles;
+    c->sel_fused = fused ? 1u : 0u;
+    if (fused && a.h_fused) cudaGraphSetConditional(a.h_fused, 1u);
+    if (!fused && a.h_multi) cudaGraphSetConditional(a.h_multi, 1u);
   }
   __syncthreads();
   if (state == kRepassHist) {
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_check2(SelArgs a) {
 __global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level) {
   __shared__ uint32_t h[kHistBins];
   const Ctl* c = a.ctl;
-  if (c->sel_prefix == 0xffffffffu) return;   // selection already decided
+  if (c->sel_fused || c->sel_prefix == 0xffffffffu) return;   // fused path, or decided
   for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x) h[i] = 0u;
   __syncthreads();
   const uint32_t nx = c->nx;
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level
 __global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) {
   __shared__ unsigned long long sh[kSelThreads];
   Ctl* c = a.ctl;
+  if (c->sel_fused) return;                   // uniform: the one-CTA kernel selects
   const bool done = c->sel_prefix == 0xffffffffu && level > 0;
   if (!done) {
     const uint64_t target = level == 0 ? (uint64_t)a.K + 1 : (uint64_t)c->sel_rank;
@@ -242,6 +249,7 @@ __device__ __forceinline__ bool kept(uint32_t key, uint32_t s2) { return key > s
 
 __global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
   Ctl* c = a.ctl;
+  if (c->sel_fused) return;
   const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
   const float mu = c->mu;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
@@ -255,6 +263,7 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
 // Exclusive scan of the per-tile counts into the next iterate's offsets.
 __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
   __shared__ unsigned long long sh[kSelThreads];
+  if (a.ctl->sel_fused) return;
   const int tid = threadIdx.x;
   const int per = (a.n_tiles + kSelThreads - 1) / kSelThreads;
   const int lo = tid * per;
@@ -288,6 +297,7 @@ __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
 // raw != 0: store b itself (the NIHT support list of the first iteration).
 __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw) {
   Ctl* c = a.ctl;
+  if (c->sel_fused) return;
   raw = raw && c->niht_first;
   const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
   const float mu = c->mu, sigma = c->sigma;
@@ -301,6 +311,152 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw
     const uint32_t pos = atomicAdd(&a.tile_cur[tile], 1u);
     a.xo_idx[pos] = idx;
     a.xo_val[pos] = raw ? b : shrink(b, sigma, a.thresh);
+  }
+}
+
+// ------------------------------------------------------------------ one-CTA selection
+// The radix select, the per-tile count, its scan and the scatter of k_sel_round /
+// k_sel_pick / k_thr_count / k_thr_scan / k_thr_scatter in one CTA, with the union's
+// keys held in shared memory: one launch instead of nine when the union (support and
+// candidates) has at most kFusedMaxUnion elements, the step is fixed and no re-pass ran.
+constexpr size_t kFusedSmem = (size_t)(kFusedMaxUnion + kHistBins + kFusedMaxTiles) * sizeof(uint32_t);
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
+  extern __shared__ uint32_t fsm[];
+  uint32_t* key = fsm;                        // union keys
+  uint32_t* h = key + kFusedMaxUnion;         // radix histogram
+  uint32_t* tcnt = h + kHistBins;             // per-tile counts, then cursors
+  __shared__ unsigned long long sh[kSelThreads];
+  __shared__ uint32_t s_jstar;
+  Ctl* c = a.ctl;
+  if (!c->sel_fused) return;                  // uniform
+  const int tid = threadIdx.x;
+  const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap);
+  const float mu = c->mu;
+  // one CTA has few threads for the latency of these loads: each thread keeps kU
+  // elements' loads in flight at a time
+  constexpr int kU = 8;
+  for (uint32_t e0 = tid; e0 < nu; e0 += kU * kSelThreads) {
+    float2 bv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t e = e0 + u * kSelThreads;
+      uint32_t idx;
+      bv[u] = e < nu ? union_b(a, e, nx, mu, &idx) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t e = e0 + u * kSelThreads;
+      if (e < nu) key[e] = key_of(bv[u]);
+    }
+  }
+  // three radix rounds (12 + 12 + 8 key bits) on the keys in shared memory
+  uint64_t target = (uint64_t)a.K + 1;
+  uint32_t prefix = 0u, s2 = 0u;
+  bool all = false;
+  for (int level = 0; level < 3; ++level) {
+    const int nb = level == 2 ? 256 : (int)kHistBins;
+    for (int i = tid; i < nb; i += kSelThreads) h[i] = 0u;
+    __syncthreads();
+    for (uint32_t e = tid; e < nu; e += kSelThreads) {
+      const uint32_t k = key[e];
+      if (k < kMinKey) continue;
+      if (level == 0) atomicAdd(&h[k >> 20], 1u);
+      else if (level == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 4095u], 1u); }
+      else if ((k >> 8) == prefix) atomicAdd(&h[k & 255u], 1u);
+    }
+    __syncthreads();
+    uint64_t above = 0;
+    const int b = find_bin(h, nb, target, &above, sh);
+    if (b < 0) {                              // fewer than K+1 nonzero magnitudes: keep all
+      all = true;
+      break;
+    }
+    target -= above;
+    prefix = level == 0 ? (uint32_t)b : (level == 1 ? ((prefix << 12) | (uint32_t)b) : prefix);
+    if (level == 2) s2 = (prefix << 8) | (uint32_t)b;
+  }
+  if (all) s2 = 0u;
+  const float sigma = all ? 0.f : sqrtf(__uint_as_float(s2));
+  // strict |b| > sigma per column tile, and the (K+1)-th element (smallest index at s2)
+  const int nt = a.n_tiles;
+  for (int i = tid; i < nt; i += kSelThreads) tcnt[i] = 0u;
+  if (tid == 0) s_jstar = 0xffffffffu;
+  __syncthreads();
+  for (uint32_t e0 = tid; e0 < nu; e0 += kU * kSelThreads) {
+    uint32_t ix[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t e = e0 + u * kSelThreads;
+      const uint32_t k = e < nu ? key[e] : 0u;
+      const bool need = e < nu && (kept(k, s2) || (k == s2 && s2 >= kMinKey));
+      ix[u] = need ? (e < nx ? a.xs_idx[e] : a.cand_idx[e - nx]) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (ix[u] == 0xffffffffu) continue;
+      const uint32_t e = e0 + u * kSelThreads;
+      if (kept(key[e], s2)) atomicAdd(&tcnt[(ix[u] % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+      else atomicMin(&s_jstar, ix[u]);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the tile counts (per-thread runs of nt/1024) into offsets
+  const int per = (nt + kSelThreads - 1) / kSelThreads;
+  const int lo = tid * per;
+  unsigned long long run = 0;
+  for (int i = 0; i < per; ++i)
+    if (lo + i < nt) run += tcnt[lo + i];
+  sh[tid] = run;
+  __syncthreads();
+  for (int off = 1; off < kSelThreads; off <<= 1) {
+    const unsigned long long add = tid >= off ? sh[tid - off] : 0ull;
+    __syncthreads();
+    sh[tid] += add;
+    __syncthreads();
+  }
+  run = tid ? sh[tid - 1] : 0ull;
+  for (int i = 0; i < per; ++i) {
+    const int k = lo + i;
+    if (k < nt) {
+      const uint32_t cnt = tcnt[k];
+      a.xo_off[k] = (uint32_t)run;
+      tcnt[k] = (uint32_t)run;                // cursor
+      run += cnt;
+    }
+  }
+  const uint32_t total = (uint32_t)sh[kSelThreads - 1];
+  if (tid == 0) a.xo_off[nt] = total;
+  __syncthreads();
+  const uint32_t jstar = s_jstar;
+  for (uint32_t e0 = tid; e0 < nu; e0 += kU * kSelThreads) {
+    uint32_t ix[kU];
+    float2 bv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint32_t e = e0 + u * kSelThreads;
+      const uint32_t k = e < nu ? key[e] : 0u;
+      const bool need = e < nu && (kept(k, s2) || (k == s2 && s2 >= kMinKey));
+      ix[u] = 0xffffffffu;
+      bv[u] = make_float2(0.f, 0.f);
+      if (need) bv[u] = union_b(a, e, nx, mu, &ix[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (ix[u] == 0xffffffffu) continue;
+      const uint32_t e = e0 + u * kSelThreads;
+      if (ix[u] == jstar) c->b_jstar = bv[u];
+      if (!kept(key[e], s2)) continue;
+      const uint32_t pos = atomicAdd(&tcnt[(ix[u] % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+      a.xo_idx[pos] = ix[u];
+      a.xo_val[pos] = shrink(bv[u], sigma, a.thresh);
+    }
+  }
+  if (tid == 0) {
+    c->sigma2_key = s2;
+    c->sigma = sigma;
+    c->jstar = jstar;
+    c->nnz = total;
   }
 }
 
@@ -505,6 +661,13 @@ cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s) { return launch_niht_mu_mode(a, 0, s); }
+cudaError_t sel_set_attributes() {
+  return cudaFuncSetAttribute(k_sel_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+}
+cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s) {
+  k_sel_fused<<<1, kSelThreads, kFusedSmem, s>>>(a);
+  return cudaGetLastError();
+}
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s) {
   k_sel_finish<<<1, kSelThreads, 0, s>>>(a);
   return cudaGetLastError();
