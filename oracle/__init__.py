@@ -11,6 +11,8 @@ with no blocking, fusion or reordering.
 
 Modules
   csa      grids, chirp-scaling phase functions H1/H2/H3, operators M and G
+  rda      the range-Doppler operator pair with truncated-sinc RCMC C and D = C^T
+           (the paper's own concrete example, Section III-C)
   ita      soft / half thresholding, the (K+1)-th largest magnitude, ITA with
            fixed or NIHT step, the autofocus loss and its gradients
   echo     exact point-target echo simulator (time domain, hyperbolic range)
