@@ -85,6 +85,16 @@ typedef struct csar_batch_s* csar_batch;
 #define CSAR_PLAN_COL_CLUSTER(p) ((uint32_t)(p) << 8)
 #define CSAR_PLAN_COL_HALF_TILE ((uint32_t)1 << 16)
 
+/* csar_plan_create flag: csar_G / csar_M use the range-Doppler operator pair of the
+ * paper's concrete example (Section III-C, Eqs. (14)-(18)) instead of the chirp-scaling
+ * one: M = range compression (range FFT, x exp(j pi f_tau^2 / K_r), range IFFT), azimuth
+ * FFT, RCMC C (8-tap truncated-sinc interpolation along range to tau + dr, dr =
+ * 2 R0 (1/D - 1) fs / c samples, Eq. (16)), x exp(j 4 pi R0 f0 D / c), azimuth IFFT;
+ * G = M^H (conjugate filters, D = C^T, reverse order; Theorem 1).  M G is close to,
+ * not exactly, the identity (the truncated interpolation is not unitary).  The ITA,
+ * autofocus and batch entry points reject such a plan (CSAR_E_UNSUPPORTED). */
+#define CSAR_PLAN_RDA ((uint32_t)1 << 17)
+
 enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };
 enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1 };
 

@@ -192,6 +192,45 @@ csar_status build_coefs_into(const csar_params& p, RowCoef* g, RowCoef* m) {
 }
 
 
+// Coefficients of the range-Doppler operator pair (Section III-C, Eqs. (14)-(18)):
+//   range filter P_tau = exp(j pi f_tau^2 / K_r): phase m^2 df^2 / (2 K_r) cycles per
+//     signed range-frequency bin m (the middle phase of a range pass; no outer phases);
+//   migration dr = (1/D - 1)(2 R_ref fs / c + j') range samples, j' = tau - N_r/2;
+//   azimuth filter P_eta = exp(j 4 pi R0 f0 D / c) = exp(j 2 pi (2 R_ref f0 D / c + j' f0 D / fs)).
+csar_status build_rda_coefs(const csar_params& p, RowCoef* rg_g, RowCoef* rg_m, RcmcCoef* rc) {
+  const double c = p.c > 0.0 ? p.c : 299792458.0;
+  const double f0 = c / p.wavelength;
+  const double kr = p.bandwidth / p.pulse_len;
+  const double df = p.fs / p.n_rg;
+  const double lim = 4194304.0;  // 2^22
+  const double cq = 0.5 * df * df / kr;
+  if (cq * (p.n_rg / 2.0) * (p.n_rg / 2.0) >= lim)
+    return fail(CSAR_E_UNSUPPORTED, "range filter phase too large for on-the-fly evaluation");
+  const PhaseCoef zero = make_coef(0.0, 0.0, 0.0, 1.0);
+  const double c0 = 2.0 * p.r0 * p.fs / c;
+  for (int k = 0; k < p.n_az; ++k) {
+    rg_m[k].pro = zero;
+    rg_m[k].mid = make_coef(0.0, 0.0, cq, 1.0);
+    rg_m[k].epi = zero;
+    rg_g[k].pro = zero;
+    rg_g[k].mid = make_coef(0.0, 0.0, cq, -1.0);
+    rg_g[k].epi = zero;
+    const int ks = k < p.n_az / 2 ? k : k - p.n_az;
+    const double fe = ks * p.prf / p.n_az;
+    const double x = c * fe / (2.0 * p.velocity * f0);
+    if (!(x * x < 1.0)) return fail(CSAR_E_UNSUPPORTED, "Doppler frequency %.6g Hz exceeds 2V/lambda", fe);
+    const double d = std::sqrt(1.0 - x * x);
+    const double alpha = 1.0 / d - 1.0;
+    split(alpha, &rc[k].al_hi, &rc[k].al_lo);
+    split(alpha * c0, &rc[k].a0_hi, &rc[k].a0_lo);
+    const double az_b = f0 * d / p.fs;
+    if (std::fabs(az_b) * (p.n_rg / 2.0) >= lim || std::fabs(alpha * c0) >= lim)
+      return fail(CSAR_E_UNSUPPORTED, "azimuth filter / migration too large (row %d)", k);
+    rc[k].az = make_coef(2.0 * p.r0 * f0 * d / c, az_b, 0.0, 1.0);
+  }
+  return CSAR_OK;
+}
+
 // Twiddle table W_8192^m, two levels (kTwLo + kTwHi entries), FP64 then rounded once.
 void build_twiddles(float2* tw) {
   const double two_pi = 6.283185307179586476925286766559;
@@ -269,6 +308,11 @@ struct csar_plan_s {
   int col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
+  // range-Doppler operator pair (CSAR_PLAN_RDA): range-filter rows and RCMC rows
+  bool rda = false;
+  RowCoef* rda_rg_g = nullptr;
+  RowCoef* rda_rg_m = nullptr;
+  RcmcCoef* rda_rcmc = nullptr;
   float2* tw = nullptr;
   Buffers b;
   cudaStream_t cap_stream = nullptr;
@@ -630,7 +674,8 @@ csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
     return fail(CSAR_E_INVALID, "mu must be finite and > 0");
   if (o->thresh != CSAR_THRESH_SOFT && o->thresh != CSAR_THRESH_HALF)
     return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT or CSAR_THRESH_HALF");
-  (void)plan;
+  if (plan && plan->rda)
+    return fail(CSAR_E_UNSUPPORTED, "the range-Doppler operator pair provides G and M only");
   return CSAR_OK;
 }
 
@@ -658,6 +703,34 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
   ColArgs c = col_args(plan);
   c.in = (const float2*)in;
   c.out = (float2*)out;
+  if (plan->rda) {
+    // M: range compression, azimuth FFT, RCMC + azimuth filter, azimuth IFFT;
+    // G: azimuth FFT, conj azimuth filter + RCMC transpose, azimuth IFFT, range pass
+    RcmcArgs r{};
+    r.data = (float2*)out;
+    r.coef = plan->rda_rcmc;
+    r.n_rows = plan->na;
+    r.nr = plan->nr;
+    r.mode = is_g ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if (is_g) {
+      e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
+      if (e == cudaSuccess) e = launch_rcmc(r, s);
+      c.in = (const float2*)out;
+      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
+      if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, plan->rda_rg_g), s);
+    } else {
+      RowArgs ra = row_args(plan, (float2*)out, plan->rda_rg_m);
+      ra.src = (const float2*)in;
+      e = launch_row(plan->nr, ra, s);
+      c.in = (const float2*)out;
+      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
+      if (e == cudaSuccess) e = launch_rcmc(r, s);
+      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G (RDA)" : "csar_M (RDA)");
+    return CSAR_OK;
+  }
   cudaError_t e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
   if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), s);
   c.in = (const float2*)out;
@@ -812,7 +885,7 @@ int32_t csar_version(void) { return 10000; }
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE))
+  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_RDA))
     return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
   const int forced_p = (int)((flags >> 8) & 0xffu);
   ColConf forced;
@@ -867,6 +940,19 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(dalloc(&plan->coef_m, plan->na));
   PK(cudaMemcpy(plan->coef_g, cg.data(), cg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
   PK(cudaMemcpy(plan->coef_m, cm.data(), cm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
+  if (flags & CSAR_PLAN_RDA) {
+    std::vector<RowCoef> rg(params->n_az), rm(params->n_az);
+    std::vector<RcmcCoef> rc(params->n_az);
+    if (csar_status st = build_rda_coefs(*params, rg.data(), rm.data(), rc.data())) return bail(st);
+    PK(rcmc_set_attributes());
+    PK(dalloc(&plan->rda_rg_g, plan->na));
+    PK(dalloc(&plan->rda_rg_m, plan->na));
+    PK(dalloc(&plan->rda_rcmc, plan->na));
+    PK(cudaMemcpy(plan->rda_rg_g, rg.data(), rg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
+    PK(cudaMemcpy(plan->rda_rg_m, rm.data(), rm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
+    PK(cudaMemcpy(plan->rda_rcmc, rc.data(), rc.size() * sizeof(RcmcCoef), cudaMemcpyHostToDevice));
+    plan->rda = true;
+  }
   {
     std::vector<float2> tw(kTwLo + kTwHi);
     build_twiddles(tw.data());
@@ -914,6 +1000,9 @@ csar_status csar_plan_destroy(csar_plan plan) {
   free_buffers(plan->b);
   if (plan->coef_g) cudaFree(plan->coef_g);
   if (plan->coef_m) cudaFree(plan->coef_m);
+  if (plan->rda_rg_g) cudaFree(plan->rda_rg_g);
+  if (plan->rda_rg_m) cudaFree(plan->rda_rg_m);
+  if (plan->rda_rcmc) cudaFree(plan->rda_rcmc);
   if (plan->tw) cudaFree(plan->tw);
   delete plan;
   return CSAR_OK;
@@ -1050,6 +1139,7 @@ csar_status csar_af_loss(csar_plan plan, const void* Y_dev, const uint32_t* mask
                          const void* X_dev, double* loss_dev, void* grad_X_dev, float* grad_theta_dev,
                          void* stream) {
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (plan->rda) return fail(CSAR_E_UNSUPPORTED, "autofocus uses the chirp-scaling operator pair");
   if (!Y_dev || !mask_dev || !theta_dev || !X_dev || !loss_dev)
     return fail(CSAR_E_INVALID, "null data pointer");
   DeviceGuard dg(plan->dev);
@@ -1069,6 +1159,7 @@ csar_status csar_af_loss(csar_plan plan, const void* Y_dev, const uint32_t* mask
 csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
                              const void* Xbar_dev, float* theta_bar_dev, void* X0bar_dev, void* stream) {
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (plan->rda) return fail(CSAR_E_UNSUPPORTED, "autofocus uses the chirp-scaling operator pair");
   if (!Y_dev || !mask_dev || !theta_dev || !Xbar_dev || !theta_bar_dev)
     return fail(CSAR_E_INVALID, "null data pointer");
   if (plan->b.ck_iters <= 0)
@@ -1100,6 +1191,7 @@ csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!params || n_patches <= 0) return fail(CSAR_E_INVALID, "need n_patches > 0 parameter sets");
+  if (flags & CSAR_PLAN_RDA) return fail(CSAR_E_UNSUPPORTED, "batches use the chirp-scaling operator pair");
   csar_batch b = new csar_batch_s();
   CK(cudaGetDevice(&b->dev));
   for (int i = 0; i < n_patches; ++i) {

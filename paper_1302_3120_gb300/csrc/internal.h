@@ -120,7 +120,8 @@ struct ColArgs {
 };
 
 struct RowArgs {
-  float2* data;             // in place, [n_rows][N_r]
+  float2* data;             // output (and input unless src is set), [n_rows][N_r]
+  const float2* src;        // if non-null, the rows are read from here instead of data
   const RowCoef* coef;      // one per row
   const float2* tw;
   const uint32_t* gate;     // if non-null, the pass runs only when *gate == gate_val
@@ -135,6 +136,23 @@ struct RowArgs {
   float* partial;
   Ctl* ctl;
   float resid_scale;
+};
+
+// Range-Doppler operator pair (rcmc.cu): per azimuth-frequency row, the migration
+// dr(tau) = alpha (c0 + j') in range samples (alpha = 1/D - 1, c0 = 2 R_ref fs / c,
+// j' = tau - N_r/2) as fp32 (hi, lo) pairs, and the azimuth matched filter's phase.
+struct RcmcCoef {
+  float al_hi, al_lo;    // alpha
+  float a0_hi, a0_lo;    // alpha * c0
+  PhaseCoef az;          // P_eta = exp(j 2 pi (A + B j'))
+};
+
+struct RcmcArgs {
+  float2* data;          // in place, [n_rows][nr]
+  const RcmcCoef* coef;  // one per row
+  int n_rows;
+  int nr;
+  int mode;              // 0: P_eta . C(data);  1: D(conj(P_eta) . data), D = C^T
 };
 
 // Column passes: a cluster of P CTAs owns col_w(N, P, E) adjacent columns; each CTA
@@ -235,6 +253,8 @@ cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s);
+cudaError_t launch_rcmc(const RcmcArgs& a, cudaStream_t s);
+cudaError_t rcmc_set_attributes();
 cudaError_t sel_set_attributes();
 
 // autofocus (autofocus.cu)

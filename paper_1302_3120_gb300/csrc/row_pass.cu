@@ -43,9 +43,10 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   const bool live = row < a.n_rows;
   const RowCoef* cp = a.coef + (live ? row : 0);
   float2* rp = a.data + (size_t)(live ? row : 0) * N;
+  const float2* sp = a.src ? a.src + (size_t)(live ? row : 0) * N : rp;
   float2 v[R];
 #pragma unroll
-  for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+  for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&sp[t + s * QR]) : make_float2(0.f, 0.f);
   if constexpr (kRowChains<N>) {
     // Gamma tables of this CTA's rows for the three phases: gam[(row*3 + phase)*R + u]
     for (int i = tid; i < WR * 3 * R; i += row_threads(N)) {
