@@ -311,6 +311,57 @@ def run_autofocus(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_operators(args, world, rank, local):
+    """Standalone operators on the 8192^2 spaceborne grid: one step = one G and one M
+    application (chirp-scaling pair, or the range-Doppler pair with sinc RCMC)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1302_3120_gb300 import build
+    build.build()
+    from paper_1302_3120_gb300 import csar
+    g = synth.spaceborne(N_AZ, N_RG)
+    rda = args.op == "rda"
+    plan = csar.csar_plan_create(g, flags=csar.PLAN_RDA if rda else 0)
+    rng = np.random.default_rng(7 + rank)
+    x = torch.from_numpy(synth.targets_over_clutter(rng, N_AZ, N_RG).astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        csar.csar_G(plan, x, y, stream=stream)
+        csar.csar_M(plan, y, x, stream=stream)
+    steps = args.steps
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(steps):
+            csar.csar_G(plan, x, y, stream=stream)
+        e[1].record(stream)
+        for _ in range(steps):
+            csar.csar_M(plan, y, x, stream=stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+    ms_g, ms_m = e[0].elapsed_time(e[1]) / steps, e[1].elapsed_time(e[2]) / steps
+    n = N_AZ * N_RG
+    # algorithmic bytes per application: column, range and column pass each read and
+    # write every element once (both pairs)
+    alg = 48.0 * n
+    peak, peak_kind = peaks()
+    gbs = alg / ((ms_g + ms_m) / 2 * 1e-3) / 1e9
+    line = {"metric": f"{'RDA' if rda else 'CSA'} operator applications/s (G and M, 8192x8192 c64)",
+            "value": 2 * steps / ((ms_g + ms_m) * steps / 1e3), "unit": "applications/s",
+            "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_g + ms_m, "G_ms": ms_g, "M_ms": ms_m, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "spaceborne 8192x8192, targets over clutter; one step = G then M",
+                       "operator": "range-Doppler, 8-tap sinc RCMC" if rda else "chirp scaling"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": gbs / peak, "alg_bytes_per_application": alg},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,8 +369,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="spaceborne8192",
-                    choices=["spaceborne8192", "batched", "autofocus"],
-                    help="spaceborne8192 (default, the headline) or the batched / autofocus rows")
+                    choices=["spaceborne8192", "batched", "autofocus", "operators"],
+                    help="spaceborne8192 (default, the headline), the batched / autofocus rows, "
+                         "or standalone G/M applications")
+    ap.add_argument("--op", default="csa", choices=["csa", "rda"],
+                    help="operator pair of --workload operators")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--size", type=int, default=8192,
@@ -342,6 +396,9 @@ def main():
         return
     if args.workload == "autofocus":
         run_autofocus(args, world, rank, local)
+        return
+    if args.workload == "operators":
+        run_operators(args, world, rank, local)
         return
 
     import torch

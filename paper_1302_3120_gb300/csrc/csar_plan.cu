@@ -197,6 +197,9 @@ csar_status build_coefs_into(const csar_params& p, RowCoef* g, RowCoef* m) {
 //     signed range-frequency bin m (the middle phase of a range pass; no outer phases);
 //   migration dr = (1/D - 1)(2 R_ref fs / c + j') range samples, j' = tau - N_r/2;
 //   azimuth filter P_eta = exp(j 4 pi R0 f0 D / c) = exp(j 2 pi (2 R_ref f0 D / c + j' f0 D / fs)).
+// rc holds 2 N_a rows: those of M, then those of G (azimuth filter conjugated).  The
+// range pass of G scatters without atomics, which needs the migration slope alpha below
+// 1/2 sample per sample (D >= 2/3; far beyond the beams the range-Doppler method serves).
 csar_status build_rda_coefs(const csar_params& p, RowCoef* rg_g, RowCoef* rg_m, RcmcCoef* rc) {
   const double c = p.c > 0.0 ? p.c : 299792458.0;
   const double f0 = c / p.wavelength;
@@ -221,12 +224,16 @@ csar_status build_rda_coefs(const csar_params& p, RowCoef* rg_g, RowCoef* rg_m, 
     if (!(x * x < 1.0)) return fail(CSAR_E_UNSUPPORTED, "Doppler frequency %.6g Hz exceeds 2V/lambda", fe);
     const double d = std::sqrt(1.0 - x * x);
     const double alpha = 1.0 / d - 1.0;
+    if (!(alpha <= 0.5))
+      return fail(CSAR_E_UNSUPPORTED, "range migration slope %.3g > 0.5 (row %d)", alpha, k);
     split(alpha, &rc[k].al_hi, &rc[k].al_lo);
     split(alpha * c0, &rc[k].a0_hi, &rc[k].a0_lo);
     const double az_b = f0 * d / p.fs;
     if (std::fabs(az_b) * (p.n_rg / 2.0) >= lim || std::fabs(alpha * c0) >= lim)
       return fail(CSAR_E_UNSUPPORTED, "azimuth filter / migration too large (row %d)", k);
     rc[k].az = make_coef(2.0 * p.r0 * f0 * d / c, az_b, 0.0, 1.0);
+    rc[p.n_az + k] = rc[k];
+    rc[p.n_az + k].az = make_coef(2.0 * p.r0 * f0 * d / c, az_b, 0.0, -1.0);
   }
   return CSAR_OK;
 }
@@ -704,30 +711,18 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
   c.in = (const float2*)in;
   c.out = (float2*)out;
   if (plan->rda) {
-    // M: range compression, azimuth FFT, RCMC + azimuth filter, azimuth IFFT;
-    // G: azimuth FFT, conj azimuth filter + RCMC transpose, azimuth IFFT, range pass
-    RcmcArgs r{};
+    // azimuth FFT, range pass (range compression, RCMC, azimuth filter), azimuth IFFT
+    RdaArgs r{};
     r.data = (float2*)out;
-    r.coef = plan->rda_rcmc;
+    r.rc = plan->rda_rcmc + (is_g ? plan->na : 0);
+    r.rg = is_g ? plan->rda_rg_g : plan->rda_rg_m;
+    r.tw = plan->tw;
     r.n_rows = plan->na;
-    r.nr = plan->nr;
-    r.mode = is_g ? 1 : 0;
-    cudaError_t e = cudaSuccess;
-    if (is_g) {
-      e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
-      if (e == cudaSuccess) e = launch_rcmc(r, s);
-      c.in = (const float2*)out;
-      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
-      if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, plan->rda_rg_g), s);
-    } else {
-      RowArgs ra = row_args(plan, (float2*)out, plan->rda_rg_m);
-      ra.src = (const float2*)in;
-      e = launch_row(plan->nr, ra, s);
-      c.in = (const float2*)out;
-      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
-      if (e == cudaSuccess) e = launch_rcmc(r, s);
-      if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
-    }
+    r.scale = 1.f / plan->nr;
+    cudaError_t e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
+    if (e == cudaSuccess) e = launch_row_rda(plan->nr, r, is_g, s);
+    c.in = (const float2*)out;
+    if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
     if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G (RDA)" : "csar_M (RDA)");
     return CSAR_OK;
   }
@@ -942,12 +937,12 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(cudaMemcpy(plan->coef_m, cm.data(), cm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
   if (flags & CSAR_PLAN_RDA) {
     std::vector<RowCoef> rg(params->n_az), rm(params->n_az);
-    std::vector<RcmcCoef> rc(params->n_az);
+    std::vector<RcmcCoef> rc(2 * (size_t)params->n_az);
     if (csar_status st = build_rda_coefs(*params, rg.data(), rm.data(), rc.data())) return bail(st);
-    PK(rcmc_set_attributes());
+    PK(rda_set_attributes(plan->nr));
     PK(dalloc(&plan->rda_rg_g, plan->na));
     PK(dalloc(&plan->rda_rg_m, plan->na));
-    PK(dalloc(&plan->rda_rcmc, plan->na));
+    PK(dalloc(&plan->rda_rcmc, 2 * (size_t)plan->na));
     PK(cudaMemcpy(plan->rda_rg_g, rg.data(), rg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
     PK(cudaMemcpy(plan->rda_rg_m, rm.data(), rm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
     PK(cudaMemcpy(plan->rda_rcmc, rc.data(), rc.size() * sizeof(RcmcCoef), cudaMemcpyHostToDevice));

@@ -138,7 +138,7 @@ struct RowArgs {
   float resid_scale;
 };
 
-// Range-Doppler operator pair (rcmc.cu): per azimuth-frequency row, the migration
+// Range-Doppler operator pair (rda_pass.cu): per azimuth-frequency row, the migration
 // dr(tau) = alpha (c0 + j') in range samples (alpha = 1/D - 1, c0 = 2 R_ref fs / c,
 // j' = tau - N_r/2) as fp32 (hi, lo) pairs, and the azimuth matched filter's phase.
 struct RcmcCoef {
@@ -147,12 +147,15 @@ struct RcmcCoef {
   PhaseCoef az;          // P_eta = exp(j 2 pi (A + B j'))
 };
 
-struct RcmcArgs {
-  float2* data;          // in place, [n_rows][nr]
-  const RcmcCoef* coef;  // one per row
+// Range pass of the range-Doppler pair, in place on [n_rows][N_r] range-Doppler rows:
+// M: P_eta . C(F_r^-1 P_tau F_r data);  G: F_r^-1 P_tau^* F_r D(conj(P_eta) . data).
+struct RdaArgs {
+  float2* data;
+  const RcmcCoef* rc;    // migration and azimuth filter, one per row
+  const RowCoef* rg;     // range filter P_tau (or its conjugate) as the middle phase
+  const float2* tw;
   int n_rows;
-  int nr;
-  int mode;              // 0: P_eta . C(data);  1: D(conj(P_eta) . data), D = C^T
+  float scale;           // 1/N_r of the range IFFT
 };
 
 // Column passes: a cluster of P CTAs owns col_w(N, P, E) adjacent columns; each CTA
@@ -253,8 +256,8 @@ cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s);
-cudaError_t launch_rcmc(const RcmcArgs& a, cudaStream_t s);
-cudaError_t rcmc_set_attributes();
+cudaError_t launch_row_rda(int nr, const RdaArgs& a, bool is_g, cudaStream_t s);
+cudaError_t rda_set_attributes(int nr);
 cudaError_t sel_set_attributes();
 
 // autofocus (autofocus.cu)

@@ -1,0 +1,262 @@
+// rda_pass.cu — the range pass of the range-Doppler operator pair (Section III-C,
+// Eqs. (14)-(18), (22)): range compression, RCMC and the azimuth matched filter in one
+// pass over the range-Doppler rows.
+//
+// Range compression acts along range with the same filter on every row, so it commutes
+// with the azimuth transforms:
+//   M = F_a^-1 P_eta C F_a F_r^-1 P_tau F_r = F_a^-1 [P_eta C F_r^-1 P_tau F_r] F_a,
+//   G = M^H                                 = F_a^-1 [F_r^-1 P_tau^* F_r D P_eta^*] F_a,
+// and each operator is a column FFT, this row pass, a column IFFT (three passes, like
+// the chirp-scaling pair).  Per azimuth-frequency row, in registers and shared memory:
+//   M:  range FFT, x P_tau, range IFFT / N_r, row staged in shared memory, every bin
+//       tau interpolated from bins b..b+7 (b = floor(tau + dr) - 3, mod N_r) with
+//       weights sinc(b + t - tau - dr), x P_eta(tau);
+//   G:  x conj(P_eta), each bin added with the same weights onto the bins it is read
+//       from in M (D = C^T), range FFT, x conj(P_tau), range IFFT / N_r.
+// The transpose scatters without atomics: the first tap b(tau) rises by at least one
+// per bin (slope 1 + alpha, alpha >= 0), so bins 16 apart write disjoint 8-bin spans.
+// Thread t holds the bins 16 t + c + j N_r / 2 (c < 16); the 16 (c, j) rounds each
+// update, in plain read-add-writes, one bin per thread, with a barrier between rounds
+// (within a half row the spans cannot wrap onto each other while alpha < 1 - 18/N_r).
+// Every accumulator therefore sums its terms in the fixed order of the rounds and G is
+// deterministic.
+// The migration dr = alpha (c0 + j') (alpha = 1/D - 1, c0 = 2 R_ref fs / c,
+// j' = tau - N_r/2) is evaluated in double-float from FP64 per-row coefficients, so its
+// fraction, which sets the weights, is accurate to ~1e-7 samples.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace csar {
+
+// First tap b of output bin tau and the fraction f: tau + dr = b + 3 + f, f in [0, 1).
+__device__ __forceinline__ int rcmc_tap(const RcmcCoef& k, int tau, int nr, float* f) {
+  const float fj = (float)(tau - nr / 2);
+  const float p = k.al_hi * fj;
+  const float e = fmaf(k.al_hi, fj, -p);              // exact error of the product
+  const float n1 = rintf(k.a0_hi), n2 = rintf(p);
+  const float fr = (k.a0_hi - n1) + (p - n2) + (k.a0_lo + e + k.al_lo * fj);
+  const float fl = floorf(fr);
+  *f = fr - fl;
+  return tau + (int)n1 + (int)n2 + (int)fl - 3;
+}
+
+// Weights w[t] = sinc(m - f), m = t - 3, from one sinpi (sin(pi (m - f)) =
+// -(-1)^m sin(pi f)) and one division: the eight reciprocals 1/(m - f) come from the
+// reciprocal of their product (batch inversion: prefix products forward, the inverse
+// carried back), a few ulp each.
+__device__ __forceinline__ void rcmc_weights(float f, float (&w)[8]) {
+  if (f <= 0.f) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) w[t] = t == 3 ? 1.f : 0.f;
+    return;
+  }
+  float d[8], pre[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) d[t] = (float)(t - 3) - f;
+  pre[0] = d[0];
+#pragma unroll
+  for (int t = 1; t < 8; ++t) pre[t] = pre[t - 1] * d[t];
+  float inv = sinpif(f) * 0.31830988618379067f / pre[7];   // (sin(pi f) / pi) / prod d
+#pragma unroll
+  for (int t = 7; t > 0; --t) {
+    const float r = inv * pre[t - 1];                      // (sin(pi f) / pi) / d[t]
+    w[t] = (t & 1) ? -r : r;                               // m = t - 3 odd <=> t even
+    inv *= d[t];
+  }
+  w[0] = inv;
+}
+
+// v[s] *= exp(j 2 pi (A + B (i0 + (s - S0) d))) for s in [S0, S1): a linear phase as
+// chains of 16 from two exact evaluations each.
+template <int R, int S0, int S1>
+__device__ __forceinline__ void phase_lin(float2 (&v)[R], const PhaseCoef& c, int i0, int d) {
+#pragma unroll
+  for (int b = S0; b < S1; b += 16) {
+    const int ib = i0 + (b - S0) * d;
+    float2 p = phase_eval(c, ib, 1.f);
+    const float2 e1 = phase_eval(c, ib + d, 1.f);
+    const float2 lam = make_float2(fmaf(e1.x, p.x, e1.y * p.y), fmaf(e1.y, p.x, -e1.x * p.y));
+    v[b] = cmul(v[b], p);
+#pragma unroll
+    for (int u = 1; u < 16 && b + u < S1; ++u) {
+      p = u == 1 ? e1 : cmul(p, lam);
+      v[b + u] = cmul(v[b + u], p);
+    }
+  }
+}
+
+// Rows of at least 1024 bins apply the range filter as chains with per-row Gamma tables
+// in shared memory; shorter rows use the re-anchored recurrence.
+template <int N>
+constexpr bool kRdaChains = N >= 1024;
+
+template <int N>
+constexpr int rda_gamma_elems() { return kRdaChains<N> ? row_w(N) * regs_for(N) : 0; }
+
+// Accumulator of the transpose: one pad slot per 16 bins, so the bins of a round (16
+// apart) fall on different banks.
+__device__ __forceinline__ int rda_pad(int i) { return i + (i >> 4); }
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
+  constexpr int WR = row_w(N);
+  constexpr int R = regs_for(N);
+  constexpr int QR = N / R;
+  constexpr int NT = row_threads(N);
+  using L = Layout<N, WR, false>;
+  static_assert(WR * (N + N / 16) <= L::kSmemElems, "accumulator rows exceed the exchange buffer");
+  extern __shared__ float2 smem[];
+  float2* sm = smem;                         // transform exchanges, and the staged rows
+  float2* tw = smem + L::kSmemElems;
+  float2* gam = tw + kTwLo + kTwHi;           // Gamma tables of the range filter, per row
+  load_twiddles(tw, a.tw);
+  const int tid = threadIdx.x;
+  const int w = tid / QR, t = tid % QR;
+  const int row = blockIdx.x * WR + w;
+  const bool live = row < a.n_rows;
+  const int rw = live ? row : 0;
+  float2* rp = a.data + (size_t)rw * N;
+  const RcmcCoef k = a.rc[rw];
+  const PhaseCoef mid = a.rg[rw].mid;
+  if constexpr (kRdaChains<N>) {
+    for (int i = tid; i < WR * R; i += NT) {
+      const int r2 = blockIdx.x * WR + i / R;
+      gam[i] = phase_gamma(a.rg[r2 < a.n_rows ? r2 : 0].mid, QR, i % R);
+    }
+  }
+  const float2* gw = gam + w * R;
+  float2 v[R];
+  if constexpr (MODE == 1) {
+    // G: bins 16 t + c + j N/2 in v[16 j + c]; conj(P_eta) (coefficients of G's rows)
+    constexpr int NJ = R / 16;
+    float2* acc = sm + w * (N + N / 16);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float4* src = reinterpret_cast<const float4*>(rp + 16 * t + j * (N / 2));
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float4 q = live ? __ldcs(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[16 * j + 2 * c] = make_float2(q.x, q.y);
+        v[16 * j + 2 * c + 1] = make_float2(q.z, q.w);
+      }
+    }
+    phase_lin<R, 0, 16>(v, k.az, 16 * t - N / 2, 1);
+    if constexpr (NJ > 1) phase_lin<R, 16, 32>(v, k.az, 16 * t, 1);
+    for (int i = t; i < N + N / 16; i += QR) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        __syncthreads();
+        const int tau = 16 * t + c + j * (N / 2);
+        float f;
+        const int b = rcmc_tap(k, tau, N, &f);
+        float wt[8];
+        rcmc_weights(f, wt);
+        const float2 x = v[16 * j + c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float2* p = acc + rda_pad((b + u) & (N - 1));
+          float2 y = *p;
+          y.x = fmaf(x.x, wt[u], y.x);
+          y.y = fmaf(x.y, wt[u], y.y);
+          *p = y;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = acc[rda_pad(t + s * QR)];
+  } else {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+    __syncthreads();   // twiddles and Gamma tables
+  }
+  // range compression: FFT, x P_tau (or conj), IFFT / N_r; range-frequency bin of v[s]
+  // is t + s QR for s < R/2 and t + (s - R) QR above
+  fft<N, false, L, false>(v, sm, tw, t, w);
+  if constexpr (kRdaChains<N>) {
+    phase_chain<R, 0, R / 2>(v, mid, t, QR, 1.f, gw);
+    phase_chain<R, R / 2, R>(v, mid, t - (R / 2) * QR, QR, 1.f, gw);
+  } else {
+    const float2 dd = phase_second_diff(mid, QR);
+    phase_ap<R, 0, R / 2>(v, mid, t, QR, 1.f, dd);
+    phase_ap<R, R / 2, R>(v, mid, t - (R / 2) * QR, QR, 1.f, dd);
+  }
+  fft<N, true, L, false>(v, sm, tw, t, w);
+  if constexpr (MODE == 0) {
+    // M: C then P_eta on the staged row
+    float2* rs = sm + w * N;
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R; ++s) rs[t + s * QR] = cscale(v[s], a.scale);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const int tau = t + s * QR;
+      float f;
+      const int b = rcmc_tap(k, tau, N, &f);
+      float wt[8];
+      rcmc_weights(f, wt);
+      float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float2 x = rs[(b + u) & (N - 1)];
+        y.x = fmaf(x.x, wt[u], y.x);
+        y.y = fmaf(x.y, wt[u], y.y);
+      }
+      v[s] = y;
+    }
+    phase_lin<R, 0, R>(v, k.az, t - N / 2, QR);
+  } else {
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = cscale(v[s], a.scale);
+  }
+  if (live) {
+#pragma unroll
+    for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
+  }
+}
+
+template <int N>
+static size_t rda_smem() {
+  using L = Layout<N, row_w(N), false>;
+  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
+         (size_t)rda_gamma_elems<N>() * sizeof(float2);
+}
+
+#define CSAR_RDA_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+cudaError_t rda_set_attributes(int nr) {
+  switch (nr) {
+#define CSAR_CASE(N)                                                                             \
+  case N: {                                                                                      \
+    cudaError_t e = cudaFuncSetAttribute(k_row_rda<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)rda_smem<N>());                                   \
+    if (e == cudaSuccess)                                                                        \
+      e = cudaFuncSetAttribute(k_row_rda<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                               (int)rda_smem<N>());                                             \
+    return e;                                                                                    \
+  }
+    CSAR_RDA_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_row_rda(int nr, const RdaArgs& a, bool is_g, cudaStream_t s) {
+  switch (nr) {
+#define CSAR_CASE(N)                                                                 \
+  case N: {                                                                          \
+    const int grid = (a.n_rows + row_w(N) - 1) / row_w(N);                           \
+    if (is_g) k_row_rda<N, 1><<<grid, row_threads(N), rda_smem<N>(), s>>>(a);        \
+    else k_row_rda<N, 0><<<grid, row_threads(N), rda_smem<N>(), s>>>(a);             \
+    return cudaGetLastError();                                                       \
+  }
+    CSAR_RDA_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace csar

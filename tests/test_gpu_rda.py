@@ -61,3 +61,28 @@ def test_rda_plan_rejects_the_ita():
     with pytest.raises(csar.CsarError) as e:
         csar.csar_solve(plan, y, dev_mask(np.ones((64, 64), bool)), 10, 2)
     assert e.value.status == 2
+
+
+def test_rda_plan_rejects_steep_migration():
+    """The transpose's atomic-free scatter needs a migration slope alpha = 1/D - 1 of at
+    most 1/2 (D >= 2/3); a PRF whose edge Doppler reaches 0.8 of 2V/lambda (D = 0.6,
+    alpha = 2/3) is refused at plan creation."""
+    import dataclasses
+    csar = lib()
+    g = dataclasses.replace(synth.airborne(64, 64), prf=0.8 * 4 * 150.0 / 0.03)
+    with pytest.raises(csar.CsarError) as e:
+        csar.csar_plan_create(g, flags=csar.PLAN_RDA)
+    assert e.value.status == 2
+
+
+def test_rda_G_is_deterministic():
+    """The transpose D = C^T sums each accumulator in a fixed order: repeated G calls
+    agree bit for bit (also on a row length with several rows per CTA)."""
+    import torch
+    csar = lib()
+    for na, nr in ((512, 8192), (256, 512)):
+        plan = csar.csar_plan_create(synth.wide_beam_lband(na, nr), flags=csar.PLAN_RDA)
+        x = dev(crand(np.random.default_rng(na), (na, nr)))
+        a = csar.csar_G(plan, x)
+        b = csar.csar_G(plan, x)
+        assert torch.equal(a, b)
