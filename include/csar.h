@@ -91,8 +91,12 @@ typedef struct csar_batch_s* csar_batch;
  * FFT, RCMC C (8-tap truncated-sinc interpolation along range to tau + dr, dr =
  * 2 R0 (1/D - 1) fs / c samples, Eq. (16)), x exp(j 4 pi R0 f0 D / c), azimuth IFFT;
  * G = M^H (conjugate filters, D = C^T, reverse order; Theorem 1).  M G is close to,
- * not exactly, the identity (the truncated interpolation is not unitary).  The ITA,
- * autofocus and batch entry points reject such a plan (CSAR_E_UNSUPPORTED). */
+ * not exactly, the identity (the truncated interpolation is not unitary).  Range
+ * compression commutes with the azimuth transforms, so each operator runs as azimuth
+ * FFT, one range pass, azimuth IFFT.  csar_ita_step and csar_solve run Algorithm 1 with
+ * this pair (the paper's CS-RDA); autofocus and batch entry points reject such a plan
+ * (CSAR_E_UNSUPPORTED), and so does plan creation when a row's migration slope
+ * 1/D - 1 exceeds 1/2 (D < 2/3). */
 #define CSAR_PLAN_RDA ((uint32_t)1 << 17)
 
 enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };

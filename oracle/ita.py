@@ -8,6 +8,10 @@ generalised to a 2-D mask S applied to a zero-filled echo), applies the matched
 filter to it, Delta X = M(R), and thresholds X + mu Delta X.  Section IV-B sets the
 threshold from the (K+1)-th largest magnitude of b = X + mu Delta X
 (lambda_i mu_i = |b|_(K+1)) and the step either fixed or adaptively (NIHT).
+
+The operator pair is a module with ``observe_G`` and ``focus_M``: the chirp-scaling
+pair (``csa``, the default) or the range-Doppler pair of Section III-C (``rda``; with
+it Algorithm 1 is the paper's CS-RDA).
 """
 from __future__ import annotations
 
@@ -15,7 +19,9 @@ import dataclasses
 
 import numpy as np
 
-from . import csa
+from . import csa, rda
+
+_OPS = {"csa": csa, "rda": rda}
 
 
 # ----------------------------------------------------------------------------- thresholds
@@ -95,7 +101,7 @@ class IterStats:
     nnz: int             # nonzeros of X^(i+1)
 
 
-def niht_step(g, mask: np.ndarray, dx: np.ndarray, support: np.ndarray) -> float:
+def niht_step(g, mask: np.ndarray, dx: np.ndarray, support: np.ndarray, ops: str = "csa") -> float:
     """Adaptive step of Section IV-B (the NIHT rule of [Blumensath2010]):
     mu_i = ||Delta X_Gamma||^2 / ||S . G(Delta X_Gamma)||^2, where Delta X_Gamma is
     Delta X restricted to Gamma.  Eq. (27) prints the reciprocal ratio; this is the
@@ -104,23 +110,24 @@ def niht_step(g, mask: np.ndarray, dx: np.ndarray, support: np.ndarray) -> float
     num = float(np.vdot(dg, dg).real)
     if num == 0.0:
         return 1.0
-    den_v = mask * csa.observe_G(g, dg)
+    den_v = mask * _OPS[ops].observe_G(g, dg)
     den = float(np.vdot(den_v, den_v).real)
     return num / den if den > 0.0 else 1.0
 
 
 def ita_iteration(g, y: np.ndarray, mask: np.ndarray, x: np.ndarray, k: int,
                   mu_mode: str = "fixed", mu: float = 1.0, kind: str = "soft",
-                  return_b: bool = False):
+                  return_b: bool = False, ops: str = "csa"):
     """One iteration of Algorithm 1 in the paper's order.  Returns (X^(i+1), stats),
     plus b = X + mu Delta X when return_b."""
-    r = mask * (y - csa.observe_G(g, x))                      # residue
-    dx = csa.focus_M(g, r)                                    # MF on residue
+    op = _OPS[ops]
+    r = mask * (y - op.observe_G(g, x))                       # residue
+    dx = op.focus_M(g, r)                                     # MF on residue
     if mu_mode == "niht":
         support = x != 0
         if not support.any():
             support = top_k_support(dx, k)
-        mu_i = niht_step(g, mask, dx, support)
+        mu_i = niht_step(g, mask, dx, support, ops)
     else:
         mu_i = float(mu)
     b = x + mu_i * dx                                         # gradient step
@@ -131,7 +138,7 @@ def ita_iteration(g, y: np.ndarray, mask: np.ndarray, x: np.ndarray, k: int,
 
 
 def ita(g, y: np.ndarray, mask: np.ndarray, k: int, iters: int, mu_mode: str = "fixed",
-        mu: float = 1.0, kind: str = "soft", x0: np.ndarray | None = None):
+        mu: float = 1.0, kind: str = "soft", x0: np.ndarray | None = None, ops: str = "csa"):
     """Algorithm 1: exactly ``iters`` iterations from X^(0) = 0 (or x0).
     Returns (X^(iters), [IterStats])."""
     x = (np.zeros((g.n_az, g.n_rg), dtype=np.complex128) if x0 is None
@@ -140,6 +147,6 @@ def ita(g, y: np.ndarray, mask: np.ndarray, k: int, iters: int, mu_mode: str = "
     y = np.asarray(y, dtype=np.complex128)
     stats = []
     for _ in range(iters):
-        x, st = ita_iteration(g, y, mask, x, k, mu_mode, mu, kind)
+        x, st = ita_iteration(g, y, mask, x, k, mu_mode, mu, kind, ops=ops)
         stats.append(st)
     return x, stats

@@ -435,6 +435,28 @@ RowArgs row_args(csar_plan plan, float2* data, const RowCoef* coef) {
   return r;
 }
 
+// Range pass of G (is_g) or M over r.data, with r's gate and residue form: the
+// chirp-scaling phases, or, on a range-Doppler plan, range compression, RCMC and the
+// azimuth filter.
+cudaError_t range_pass(csar_plan plan, const RowArgs& r, bool is_g, cudaStream_t s) {
+  if (!plan->rda) return launch_row(plan->nr, r, s);
+  if (r.src || (is_g && r.yf)) return cudaErrorInvalidValue;
+  RdaArgs a{};
+  a.data = r.data;
+  a.rc = plan->rda_rcmc + (is_g ? plan->na : 0);
+  a.rg = is_g ? plan->rda_rg_g : plan->rda_rg_m;
+  a.tw = r.tw;
+  a.gate = r.gate;
+  a.gate_val = r.gate_val;
+  a.n_rows = r.n_rows;
+  a.scale = r.scale;
+  a.yf = r.yf;
+  a.partial = r.partial;
+  a.ctl = r.ctl;
+  a.resid_scale = r.resid_scale;
+  return launch_row_rda(plan->nr, a, is_g, s);
+}
+
 SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   const Buffers& b = plan->b;
   const int nxt = 1 - cur;
@@ -539,7 +561,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(launch_sparse_dft(na, c, plan->col_tile, s));
   LK(launch_col(na, plan->col, COL_SPARSE_FWD, c, nt, s));
   LK(mark(1));
-  LK(launch_row(nr, row_args(plan, b.z, plan->coef_g), s));
+  LK(range_pass(plan, row_args(plan, b.z, plan->coef_g), true, s));
   LK(mark(2));
   // residue r = S.(Y - G(X)), produced as F_a r = F_a(S.Y) - F_a(S.G(X)): this column
   // pass forms F_a(S.G(X)), the next range pass subtracts it from F_a(S.Y)
@@ -555,7 +577,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   rm.partial = b.partial;
   rm.ctl = b.ctl;
   rm.resid_scale = 1.0f / (float)na;
-  LK(launch_row(nr, rm, s));
+  LK(range_pass(plan, rm, false, s));
   LK(mark(4));
   // Delta X = F_a^-1: support values, histogram, candidates
   LK(launch_col(na, plan->col, COL_SELECT, c, nt, s));
@@ -597,7 +619,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 0u;
-    LK(launch_row(nr, r, s));
+    LK(range_pass(plan, r, true, s));
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
@@ -636,7 +658,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 1u;
-    LK(launch_row(nr, r, s));
+    LK(range_pass(plan, r, true, s));
     g.in = b.z;
     g.mask = mask;
     g.partial = b.partial_norm;
@@ -681,8 +703,6 @@ csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
     return fail(CSAR_E_INVALID, "mu must be finite and > 0");
   if (o->thresh != CSAR_THRESH_SOFT && o->thresh != CSAR_THRESH_HALF)
     return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT or CSAR_THRESH_HALF");
-  if (plan && plan->rda)
-    return fail(CSAR_E_UNSUPPORTED, "the range-Doppler operator pair provides G and M only");
   return CSAR_OK;
 }
 
@@ -692,7 +712,7 @@ cudaError_t dense_op(csar_plan plan, const float2* in, float2* out, bool is_g, c
   c.in = in;
   c.out = out;
   LK(launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s));
-  LK(launch_row(plan->nr, row_args(plan, out, is_g ? plan->coef_g : plan->coef_m), s));
+  LK(range_pass(plan, row_args(plan, out, is_g ? plan->coef_g : plan->coef_m), is_g, s));
   c.in = out;
   return launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
 }
@@ -710,24 +730,9 @@ csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* s
   ColArgs c = col_args(plan);
   c.in = (const float2*)in;
   c.out = (float2*)out;
-  if (plan->rda) {
-    // azimuth FFT, range pass (range compression, RCMC, azimuth filter), azimuth IFFT
-    RdaArgs r{};
-    r.data = (float2*)out;
-    r.rc = plan->rda_rcmc + (is_g ? plan->na : 0);
-    r.rg = is_g ? plan->rda_rg_g : plan->rda_rg_m;
-    r.tw = plan->tw;
-    r.n_rows = plan->na;
-    r.scale = 1.f / plan->nr;
-    cudaError_t e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
-    if (e == cudaSuccess) e = launch_row_rda(plan->nr, r, is_g, s);
-    c.in = (const float2*)out;
-    if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
-    if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G (RDA)" : "csar_M (RDA)");
-    return CSAR_OK;
-  }
   cudaError_t e = launch_col(plan->na, plan->col, COL_FWD, c, plan->n_tiles, s);
-  if (e == cudaSuccess) e = launch_row(plan->nr, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), s);
+  if (e == cudaSuccess)
+    e = range_pass(plan, row_args(plan, (float2*)out, is_g ? plan->coef_g : plan->coef_m), is_g, s);
   c.in = (const float2*)out;
   if (e == cudaSuccess) e = launch_col(plan->na, plan->col, COL_INV, c, plan->n_tiles, s);
   if (e != cudaSuccess) return cuda_fail(e, is_g ? "csar_G" : "csar_M");
@@ -1113,6 +1118,7 @@ csar_status csar_af_solve(csar_plan plan, const void* Y_dev, const uint32_t* mas
                           void* X_dev, const csar_opts* opts, int32_t checkpoint, void* stream) {
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (!theta_dev) return fail(CSAR_E_INVALID, "theta is NULL");
+  if (plan->rda) return fail(CSAR_E_UNSUPPORTED, "autofocus uses the chirp-scaling operator pair");
   if (csar_status st = check_opts(plan, opts, true)) return st;
   if (checkpoint && (opts->thresh != CSAR_THRESH_SOFT || opts->mu_mode != CSAR_MU_FIXED))
     return fail(CSAR_E_UNSUPPORTED, "the autofocus backward covers soft thresholding with a fixed step");

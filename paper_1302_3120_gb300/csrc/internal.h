@@ -149,13 +149,20 @@ struct RcmcCoef {
 
 // Range pass of the range-Doppler pair, in place on [n_rows][N_r] range-Doppler rows:
 // M: P_eta . C(F_r^-1 P_tau F_r data);  G: F_r^-1 P_tau^* F_r D(conj(P_eta) . data).
+// gate and the residue form (M only) act as in RowArgs.
 struct RdaArgs {
   float2* data;
   const RcmcCoef* rc;    // migration and azimuth filter, one per row
   const RowCoef* rg;     // range filter P_tau (or its conjugate) as the middle phase
   const float2* tw;
+  const uint32_t* gate;
+  uint32_t gate_val;
   int n_rows;
   float scale;           // 1/N_r of the range IFFT
+  const float2* yf;
+  float* partial;
+  Ctl* ctl;
+  float resid_scale;
 };
 
 // Column passes: a cluster of P CTAs owns col_w(N, P, E) adjacent columns; each CTA

@@ -7,7 +7,9 @@
 //   M = F_a^-1 P_eta C F_a F_r^-1 P_tau F_r = F_a^-1 [P_eta C F_r^-1 P_tau F_r] F_a,
 //   G = M^H                                 = F_a^-1 [F_r^-1 P_tau^* F_r D P_eta^*] F_a,
 // and each operator is a column FFT, this row pass, a column IFFT (three passes, like
-// the chirp-scaling pair).  Per azimuth-frequency row, in registers and shared memory:
+// the chirp-scaling pair).  In the ITA the pass of M also takes the residue form of
+// the chirp-scaling range pass (F_a r = F_a(S.Y) - input, with the partial sums of
+// |F_a r|^2).  Per azimuth-frequency row, in registers and shared memory:
 //   M:  range FFT, x P_tau, range IFFT / N_r, row staged in shared memory, every bin
 //       tau interpolated from bins b..b+7 (b = floor(tau + dr) - 3, mod N_r) with
 //       weights sinc(b + t - tau - dr), x P_eta(tau);
@@ -15,7 +17,7 @@
 //       from in M (D = C^T), range FFT, x conj(P_tau), range IFFT / N_r.
 // The transpose scatters without atomics: the first tap b(tau) rises by at least one
 // per bin (slope 1 + alpha, alpha >= 0), so bins 16 apart write disjoint 8-bin spans.
-// Thread t holds the bins 16 t + c + j N_r / 2 (c < 16); the 16 (c, j) rounds each
+// Thread t holds the bins 16 t + c + j N_r / 2 (c < 16); the rounds (c, j) each
 // update, in plain read-add-writes, one bin per thread, with a barrier between rounds
 // (within a half row the spans cannot wrap onto each other while alpha < 1 - 18/N_r).
 // Every accumulator therefore sums its terms in the fixed order of the rounds and G is
@@ -106,9 +108,11 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   using L = Layout<N, WR, false>;
   static_assert(WR * (N + N / 16) <= L::kSmemElems, "accumulator rows exceed the exchange buffer");
   extern __shared__ float2 smem[];
+  if (a.gate && *a.gate != a.gate_val) return;
   float2* sm = smem;                         // transform exchanges, and the staged rows
   float2* tw = smem + L::kSmemElems;
-  float2* gam = tw + kTwLo + kTwHi;           // Gamma tables of the range filter, per row
+  float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);   // 32 floats
+  float2* gam = tw + kTwLo + kTwHi + 16;      // Gamma tables of the range filter, per row
   load_twiddles(tw, a.tw);
   const int tid = threadIdx.x;
   const int w = tid / QR, t = tid % QR;
@@ -170,6 +174,35 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   } else {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
+    if (a.yf) {
+      // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
+      const float2* yp = a.yf + (size_t)rw * N;
+      float sq = 0.f;
+      bool bad = false;
+#pragma unroll
+      for (int g0 = 0; g0 < R; g0 += 8) {
+        float2 y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          v[g0 + j] = csub(y[j], v[g0 + j]);
+          sq += cabs2(v[g0 + j]);
+          bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
+        }
+      }
+      if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if ((tid & 31) == 0) red[tid >> 5] = sq;
+      __syncthreads();
+      if (tid == 0) {
+        float tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) tot += red[i];
+        a.partial[blockIdx.x] = tot * a.resid_scale;
+      }
+    }
     __syncthreads();   // twiddles and Gamma tables
   }
   // range compression: FFT, x P_tau (or conj), IFFT / N_r; range-frequency bin of v[s]
@@ -221,7 +254,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
 template <int N>
 static size_t rda_smem() {
   using L = Layout<N, row_w(N), false>;
-  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
+  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi + 16) * sizeof(float2) +
          (size_t)rda_gamma_elems<N>() * sizeof(float2);
 }
 

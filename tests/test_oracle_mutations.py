@@ -114,7 +114,7 @@ ITA_PINS = [
 _soft, _half, _kth, _niht = ita.soft_threshold, ita.half_threshold, ita.kth_largest_magnitude, ita.niht_step
 
 
-def _ita_iteration_unmasked(g, y, mask, x, k, mu_mode="fixed", mu=1.0, kind="soft"):
+def _ita_iteration_unmasked(g, y, mask, x, k, mu_mode="fixed", mu=1.0, kind="soft", ops="csa"):
     r = y - csa.observe_G(g, x)
     b = x + mu * csa.focus_M(g, r)
     s = _kth(b, k)
@@ -127,7 +127,7 @@ ITA_MUTATIONS = {
                                    lambda b, s: np.where(np.abs(b) > s, np.abs(b) - s, 0).astype(complex)),
     "half threshold wrong angle": ("half_lambda_mu", lambda s: np.sqrt(96.0) / 9.0 * s),
     "K-th instead of (K+1)-th": ("kth_largest_magnitude", lambda b, k: _kth(b, max(k - 1, 0))),
-    "NIHT ratio inverted": ("niht_step", lambda g, m, dx, sup: 1.0 / _niht(g, m, dx, sup)),
+    "NIHT ratio inverted": ("niht_step", lambda g, m, dx, sup, ops="csa": 1.0 / _niht(g, m, dx, sup, ops)),
     "mask dropped from residue": ("ita_iteration", _ita_iteration_unmasked),
 }
 
