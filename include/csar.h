@@ -100,7 +100,7 @@ typedef struct csar_batch_s* csar_batch;
 #define CSAR_PLAN_RDA ((uint32_t)1 << 17)
 
 enum { CSAR_MU_FIXED = 0, CSAR_MU_NIHT = 1 };
-enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1 };
+enum { CSAR_THRESH_SOFT = 0, CSAR_THRESH_HALF = 1, CSAR_THRESH_HARD = 2 };
 
 /* Options of the iterative thresholding algorithm (Algorithm 1, Section IV-B). */
 typedef struct {
@@ -108,7 +108,8 @@ typedef struct {
   int32_t iters;      /* number of iterations I (csar_solve)                           */
   int32_t mu_mode;    /* CSAR_MU_FIXED or CSAR_MU_NIHT (adaptive step)                 */
   float mu;           /* fixed step (CSAR_MU_FIXED); must be > 0                       */
-  int32_t thresh;     /* CSAR_THRESH_SOFT (q = 1) or CSAR_THRESH_HALF (q = 1/2)        */
+  int32_t thresh;     /* CSAR_THRESH_SOFT (q = 1), CSAR_THRESH_HALF (q = 1/2) or
+                         CSAR_THRESH_HARD (q = 0: b kept where |b| > sigma)           */
 } csar_opts;
 
 /* Per-iteration diagnostics, host arrays of length >= opts.iters (any may be NULL). */

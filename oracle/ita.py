@@ -64,11 +64,21 @@ def half_threshold(b: np.ndarray, sigma: float) -> np.ndarray:
     return out
 
 
+def hard_threshold(b: np.ndarray, sigma: float) -> np.ndarray:
+    """Hard thresholding (q = 0, Section II-B): the global minimiser of
+    |x - b|^2 + lambda mu [x != 0] with lambda mu = sigma^2 keeps b where |b| > sigma
+    and is 0 elsewhere (cost sigma^2 against |b|^2)."""
+    b = np.asarray(b, dtype=np.complex128)
+    return np.where(np.abs(b) > sigma, b, 0)
+
+
 def threshold(b: np.ndarray, sigma: float, kind: str) -> np.ndarray:
     if kind == "soft":
         return soft_threshold(b, sigma)
     if kind == "half":
         return half_threshold(b, sigma)
+    if kind == "hard":
+        return hard_threshold(b, sigma)
     raise ValueError(kind)
 
 

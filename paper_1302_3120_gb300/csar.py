@@ -19,7 +19,7 @@ CSAR_OK = 0
 STATUS_NAMES = {0: "CSAR_OK", 1: "CSAR_E_INVALID", 2: "CSAR_E_UNSUPPORTED", 3: "CSAR_E_OOM",
                 4: "CSAR_E_CUDA", 5: "CSAR_E_TIMEOUT", 6: "CSAR_E_NONFINITE", 7: "CSAR_E_INTERNAL"}
 MU_MODES = {"fixed": 0, "niht": 1}
-THRESH = {"soft": 0, "half": 1}
+THRESH = {"soft": 0, "half": 1, "hard": 2}
 N_PASSES = 6
 PASS_NAMES = ("C1_sparse_fft", "R1_range_G", "C2_residue", "R2_range_M", "C3_select", "select_threshold")
 

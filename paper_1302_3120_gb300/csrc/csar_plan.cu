@@ -701,8 +701,8 @@ csar_status check_opts(csar_plan plan, const csar_opts* o, bool need_iters) {
     return fail(CSAR_E_INVALID, "mu_mode must be CSAR_MU_FIXED or CSAR_MU_NIHT");
   if (o->mu_mode == CSAR_MU_FIXED && !(o->mu > 0.f && std::isfinite(o->mu)))
     return fail(CSAR_E_INVALID, "mu must be finite and > 0");
-  if (o->thresh != CSAR_THRESH_SOFT && o->thresh != CSAR_THRESH_HALF)
-    return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT or CSAR_THRESH_HALF");
+  if (o->thresh != CSAR_THRESH_SOFT && o->thresh != CSAR_THRESH_HALF && o->thresh != CSAR_THRESH_HARD)
+    return fail(CSAR_E_INVALID, "thresh must be CSAR_THRESH_SOFT, CSAR_THRESH_HALF or CSAR_THRESH_HARD");
   return CSAR_OK;
 }
 

@@ -238,7 +238,7 @@ struct SelArgs {
   int nr;
   int col_tile;               // columns per column-pass tile
   int n_tiles;
-  int thresh;                 // 0 soft, 1 half
+  int thresh;                 // 0 soft, 1 half, 2 hard
   int mu_mode;                // 0 fixed, 1 NIHT
   float mu_fixed;
   // conditional graph nodes of the re-passes (0 when not captured): sel_check sets

@@ -1,5 +1,5 @@
 // select.cu — the threshold of Section IV-B: sigma = |b|_(K+1), the (K+1)-th largest
-// magnitude of b = X + mu Delta X, and the complex soft / half shrinkage of b.
+// magnitude of b = X + mu Delta X, and the complex soft / half / hard shrinkage of b.
 //
 // The column pass COL_SELECT has already (a) recorded Delta X on the support of the
 // current K-sparse iterate and (b) histogrammed |Delta X|^2 of every off-support
@@ -57,7 +57,9 @@ __device__ __forceinline__ uint32_t union_size(const Ctl* c, uint32_t cap) {
 //   half (q = 1/2, the L_1/2 thresholding of [Xu2010]) with lambda mu chosen so that
 //   the jump point equals sigma: b (2/3)(1 + cos(2pi/3 - (2/3) acos(c (3 sigma/|b|)^1.5))),
 //   c = sqrt(96)/72.
+//   hard (q = 0): b unchanged.
 __device__ __forceinline__ float2 shrink(float2 b, float sigma, int kind) {
+  if (kind == 2) return b;
   const float m = sqrtf(cabs2(b));
   float f;
   if (kind == 0) {

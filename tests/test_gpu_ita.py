@@ -40,6 +40,7 @@ def _problem(seed, na=256, nr=256, frac=0.01, rate=0.5, geom=synth.airborne, noi
 @pytest.mark.parametrize("mu_mode,mu,kind,x0", [
     ("fixed", 1.0, "soft", "sparse"), ("fixed", 0.7, "half", "sparse"),
     ("niht", 1.0, "soft", "sparse"), ("niht", 1.0, "half", "zero"), ("fixed", 1.3, "soft", "zero"),
+    ("fixed", 1.0, "hard", "sparse"), ("niht", 1.0, "hard", "zero"),
 ])
 @pytest.mark.parametrize("shape", [(256, 256), (64, 512), (1024, 128)])
 def test_single_iteration(mu_mode, mu, kind, x0, shape):
@@ -88,23 +89,29 @@ def test_config1_point_targets_solve():
     assert np.max(np.abs(st["resid_sq"] - res_ref) / res_ref) < 1e-3
 
 
-@pytest.mark.parametrize("mu_mode,kind", [("fixed", "soft"), ("niht", "soft"), ("fixed", "half")])
+@pytest.mark.parametrize("mu_mode,kind", [("fixed", "soft"), ("niht", "soft"), ("fixed", "half"),
+                                          ("niht", "hard")])
 def test_distributed_scene_solve(mu_mode, kind):
     """512^2 airborne, 1% Rayleigh scene, G(X) echo + 20 dB noise, 50% sampling,
     K = 1% of n, 30 iterations."""
     csar = lib()
     g, xt, y, mask = _problem(21, 512, 512, noise_db=20.0)
     K = int(round(0.01 * 512 * 512))
-    x_ref, st_ref = ita.ita(g, y, mask, K, 30, mu_mode=mu_mode, kind=kind)
+    iters = 30
+    x_ref, st_ref = ita.ita(g, y, mask, K, iters, mu_mode=mu_mode, kind=kind)
     plan = csar.csar_plan_create(g)
-    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 30, mu_mode=mu_mode, thresh=kind,
+    X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, iters, mu_mode=mu_mode, thresh=kind,
                             stats=True)
     xg = host(X)
     assert metrics.rel_l2(xg, x_ref) < 1e-3
     assert np.all(st["nnz"] <= K)
     if mu_mode == "niht":
-        mu_ref = np.array([s_.mu for s_ in st_ref])
-        assert np.max(np.abs(st["mu"] - mu_ref) / mu_ref) < 1e-3
+        # with hard thresholding the support-restricted gradient Delta X_Gamma vanishes
+        # at a fixed point (in the oracle 6e-2 of |X| after one iteration, 4e-5 after
+        # five, 7e-9 after eleven), so later NIHT steps are ratios of fp32 rounding
+        n_mu = 5 if kind == "hard" else iters
+        mu_ref = np.array([s_.mu for s_ in st_ref])[:n_mu]
+        assert np.max(np.abs(st["mu"][:n_mu] - mu_ref) / mu_ref) < 1e-3
 
 
 def test_degenerate_cases():

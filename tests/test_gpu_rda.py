@@ -78,7 +78,7 @@ def _rda_problem(seed, na, nr, frac=0.01, rate=0.5, geom=synth.airborne):
 
 
 @pytest.mark.parametrize("mu_mode,mu,kind", [("fixed", 1.0, "soft"), ("niht", 1.0, "soft"),
-                                             ("fixed", 0.7, "half")])
+                                             ("fixed", 0.7, "half"), ("niht", 1.0, "hard")])
 @pytest.mark.parametrize("shape", [(256, 256), (64, 512), (1024, 128)])
 def test_rda_single_iteration(mu_mode, mu, kind, shape):
     """One iteration of Algorithm 1 with the range-Doppler pair (CS-RDA) from a sparse

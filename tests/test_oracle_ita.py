@@ -48,6 +48,21 @@ def test_half_threshold_is_global_minimiser_by_brute_force():
     assert abs(ita.half_threshold(np.array([1.0 + 0j]), s1)[0].real - 0.70152) < 1e-5
 
 
+def test_hard_threshold_is_l0_prox_by_brute_force():
+    """hard(b, s) minimises |x - b|^2 + s^2 [x != 0] over a fine complex grid that
+    contains b itself (the minimiser is b or 0)."""
+    rng = np.random.default_rng(5)
+    g = np.linspace(-3, 3, 601)
+    xr, xi = np.meshgrid(g, g, indexing="ij")
+    for _ in range(8):
+        b = complex(rng.uniform(-2.5, 2.5), rng.uniform(-2.5, 2.5))
+        s = rng.uniform(0.1, 3.0)
+        xc = np.append((xr + 1j * xi).reshape(-1), b)
+        obj = np.abs(xc - b) ** 2 + s ** 2 * (xc != 0)
+        best = xc[np.argmin(obj)]
+        assert abs(ita.hard_threshold(np.array([b]), s)[0] - best) < 1e-12
+
+
 def test_half_threshold_zero_sigma_is_identity():
     rng = np.random.default_rng(5)
     b = _rand(rng, 50)
@@ -70,7 +85,7 @@ def test_kth_largest_against_counting(k):
 
 # ----------------------------------------------------------------------------- ITA
 
-@pytest.mark.parametrize("kind", ["soft", "half"])
+@pytest.mark.parametrize("kind", ["soft", "half", "hard"])
 def test_full_sampling_closed_form(kind):
     """With S = 1 and mu = 1, M G = I gives B = X + M(Y - G X) = M(Y) at every
     iteration, so every iterate equals T_sigma(M(Y)) with sigma = |M Y|_(K+1)."""

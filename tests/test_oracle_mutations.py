@@ -105,6 +105,7 @@ def test_operator_mutation_is_caught(name, monkeypatch):
 ITA_PINS = [
     ita_pins.test_soft_threshold_is_prox_by_brute_force,
     ita_pins.test_half_threshold_is_global_minimiser_by_brute_force,
+    ita_pins.test_hard_threshold_is_l0_prox_by_brute_force,
     lambda: ita_pins.test_kth_largest_against_counting(7),
     lambda: ita_pins.test_full_sampling_closed_form("soft"),
     ita_pins.test_first_iterate_is_threshold_of_masked_mf,
@@ -112,6 +113,7 @@ ITA_PINS = [
 ]
 
 _soft, _half, _kth, _niht = ita.soft_threshold, ita.half_threshold, ita.kth_largest_magnitude, ita.niht_step
+_hard = ita.hard_threshold
 
 
 def _ita_iteration_unmasked(g, y, mask, x, k, mu_mode="fixed", mu=1.0, kind="soft", ops="csa"):
@@ -126,6 +128,7 @@ ITA_MUTATIONS = {
     "soft threshold drops phase": ("soft_threshold",
                                    lambda b, s: np.where(np.abs(b) > s, np.abs(b) - s, 0).astype(complex)),
     "half threshold wrong angle": ("half_lambda_mu", lambda s: np.sqrt(96.0) / 9.0 * s),
+    "hard threshold keeps |b| >= sigma / 2": ("hard_threshold", lambda b, s: _hard(b, s / 2)),
     "K-th instead of (K+1)-th": ("kth_largest_magnitude", lambda b, k: _kth(b, max(k - 1, 0))),
     "NIHT ratio inverted": ("niht_step", lambda g, m, dx, sup, ops="csa": 1.0 / _niht(g, m, dx, sup, ops)),
     "mask dropped from residue": ("ita_iteration", _ita_iteration_unmasked),
