@@ -71,7 +71,7 @@ typedef struct {
   double bandwidth;    /* chirp bandwidth B [Hz] (up-chirp)                          */
   double pulse_len;    /* pulse duration T_p [s]                                     */
   double fs;           /* range sampling rate [Hz]                                   */
-  double antenna_len;  /* La [m]; not used by G or M (kept for completeness)         */
+  double antenna_len;  /* La [m]; used only by the echo simulator csar_echo_points       */
   double c;            /* speed of light [m/s]; 0 selects 299792458                  */
 } csar_params;
 
@@ -225,6 +225,25 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
  * then the three passes). */
 csar_status csar_G_noalloc(const csar_params* params, const void* x_dev, void* y_dev,
                            void* stream);
+
+/* ---- Scene simulator ----------------------------------------------------------- */
+
+/* Raw stripmap echo of point targets on image pixels from the exact observation model
+ * (Section V-A: time-domain echoes from the exact slant range), computed on the GPU in
+ * FP64 geometry: target k at pixel (rows[k], cols[k]) has azimuth time
+ * (rows[k] - N_a/2)/PRF and closest range R_t = c tau_cols[k] / 2, tau_j =
+ * 2 r0/c + (j - N_r/2)/fs; its echo at pulse i, bin j is
+ *   a_k rect(delay/T_p) rect((eta_i - eta_k)/T_a) exp(-j 4 pi R / lambda + j pi K_r delay^2),
+ *   R = sqrt(R_t^2 + V^2 (eta_i - eta_k)^2), delay = tau_j - 2R/c,
+ *   T_a = 0.886 lambda R_t / (La V), K_r = bandwidth / pulse_len, windows closed.
+ * rows, cols: host int32 arrays of `count` (0 <= count <= 2^24) pixels on the grid;
+ * amp: host float array of 2*count (re, im); echo_dev: device [N_a][N_r] complex64,
+ * overwritten (accumulate = 0) or added to.  Needs antenna_len > 0.  No plan; the
+ * target list is copied into stream-ordered device memory (cudaMallocAsync) and freed
+ * after the launch; the host arrays may be reused as soon as the call returns. */
+csar_status csar_echo_points(const csar_params* params, const int32_t* rows, const int32_t* cols,
+                             const float* amp, int64_t count, void* echo_dev, int32_t accumulate,
+                             void* stream);
 
 /* ---- Batches of independent patches (uneven sizes) -------------------------------- */
 

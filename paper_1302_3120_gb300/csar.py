@@ -55,7 +55,7 @@ EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_it
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
            "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
-           "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout")
+           "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout", "csar_echo_points")
 
 
 def _load() -> ctypes.CDLL:
@@ -85,13 +85,14 @@ def _load() -> ctypes.CDLL:
     lib.csar_batch_check.argtypes = [vp]
     lib.csar_autotune.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(i32)]
     lib.csar_selftest_wait_timeout.argtypes = [i32]
+    lib.csar_echo_points.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int64, vp, i32, vp]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
                  "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
                  "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc",
                  "csar_batch_create", "csar_batch_destroy", "csar_solve_batched", "csar_batch_check",
-                 "csar_autotune"):
+                 "csar_autotune", "csar_echo_points"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -190,6 +191,26 @@ def csar_G_noalloc(geometry, x, y=None, stream=None):
     _need(y, torch.complex64, n, "y")
     _check(lib.csar_G_noalloc(ctypes.byref(p), _ptr(x), _ptr(y), _stream(stream)), "csar_G_noalloc")
     return y
+
+
+def csar_echo_points(geometry, rows, cols, amps, out=None, accumulate: bool = False, stream=None):
+    """Raw echo [n_az, n_rg] complex64 (CUDA tensor) of point targets on image pixels
+    (rows, cols; complex amplitudes amps) from the exact stripmap model; written into
+    ``out`` (or added to it with accumulate=True)."""
+    import torch
+    p = params_of(geometry)
+    rows = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)
+    cols = np.ascontiguousarray(cols, dtype=np.int32).reshape(-1)
+    a = np.ascontiguousarray(np.asarray(amps, dtype=np.complex64).reshape(-1)).view(np.float32)
+    if not (rows.size == cols.size == a.size // 2):
+        raise ValueError("rows, cols and amps must have the same length")
+    if out is None:
+        out = torch.empty((p.n_az, p.n_rg), dtype=torch.complex64, device="cuda")
+    _need(out, torch.complex64, p.n_az * p.n_rg, "out")
+    _check(lib.csar_echo_points(ctypes.byref(p), rows.ctypes.data, cols.ctypes.data, a.ctypes.data,
+                                rows.size, _ptr(out), int(bool(accumulate)), _stream(stream)),
+           "csar_echo_points")
+    return out
 
 
 def csar_M(plan: Plan, y, x=None, stream=None):
