@@ -80,10 +80,13 @@ typedef struct csar_batch_s* csar_batch;
 
 /* csar_plan_create flags: force the column-pass cluster size (CTAs per column tile,
  * 1..16, power of two; 0 = the autotuned or default choice), and/or column-pass CTAs
- * of 4096 complex values (four per SM, half-width tiles) instead of 8192 (two per SM).
- * A configuration that is not built for n_az gives CSAR_E_UNSUPPORTED. */
+ * of 4096 complex values (four per SM, half-width tiles) or of 16384 (one per SM,
+ * double-width tiles: wider row segments per memory request) instead of 8192 (two per
+ * SM).  A configuration that is not built for n_az gives CSAR_E_UNSUPPORTED, and so do
+ * both tile flags together. */
 #define CSAR_PLAN_COL_CLUSTER(p) ((uint32_t)(p) << 8)
 #define CSAR_PLAN_COL_HALF_TILE ((uint32_t)1 << 16)
+#define CSAR_PLAN_COL_WIDE_TILE ((uint32_t)1 << 18)
 
 /* csar_plan_create flag: csar_G / csar_M use the range-Doppler operator pair of the
  * paper's concrete example (Section III-C, Eqs. (14)-(18)) instead of the chirp-scaling
@@ -268,7 +271,7 @@ csar_status csar_batch_check(csar_batch batch);
 /* Autotuner: times `iters` ITA iterations on synthetic data for every column-pass
  * configuration available for (n_az, n_rg), keeps the fastest for plans created
  * afterwards in this process (and in the file named by CSAR_TUNE_FILE, if set), and
- * returns it in *chosen_cluster.  Both CTA sizes (CSAR_PLAN_COL_HALF_TILE or not) are
+ * returns it in *chosen_cluster.  Every CTA size (half, full and wide tiles) is
  * tried; *chosen_cluster reports the cluster size of the chosen configuration.
  * Synchronises the device; allocates temporaries. */
 csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster);

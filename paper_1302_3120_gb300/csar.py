@@ -477,5 +477,7 @@ def plan_col_cluster(p: int) -> int:
 
 # csar_plan_create flag: column-pass CTAs of 4096 complex values (half-width tiles)
 PLAN_COL_HALF_TILE = 1 << 16
+# csar_plan_create flag: column-pass CTAs of 16384 complex values (double-width tiles)
+PLAN_COL_WIDE_TILE = 1 << 18
 # csar_plan_create flag: G / M are the range-Doppler operator pair with sinc RCMC
 PLAN_RDA = 1 << 17

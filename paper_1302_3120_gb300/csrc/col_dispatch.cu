@@ -15,6 +15,7 @@ namespace csar {
 #define CSAR_COL_CONFIGS(X)                                                                   \
   X(8192, 1, 8192) X(8192, 2, 8192) X(8192, 4, 8192) X(8192, 8, 8192) X(8192, 16, 8192)       \
   X(8192, 2, 4096) X(8192, 4, 4096) X(8192, 8, 4096) X(8192, 16, 4096)                         \
+  X(8192, 4, 16384) X(8192, 8, 16384)                                                          \
   X(4096, 1, 8192) X(4096, 2, 8192) X(4096, 4, 8192) X(4096, 8, 8192)                          \
   X(4096, 1, 4096) X(4096, 2, 4096) X(4096, 4, 4096) X(4096, 8, 4096)                          \
   X(2048, 1, 8192) X(2048, 2, 8192) X(2048, 4, 8192)                                           \

@@ -885,13 +885,17 @@ int32_t csar_version(void) { return 10000; }
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_RDA))
+  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_RDA))
     return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
+  const uint32_t tile_flags = flags & (CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE);
+  if (tile_flags == (CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE))
+    return fail(CSAR_E_UNSUPPORTED, "half and wide column tiles together");
   const int forced_p = (int)((flags >> 8) & 0xffu);
   ColConf forced;
   forced.p = forced_p;
-  forced.e = (flags & CSAR_PLAN_COL_HALF_TILE) ? kColCtaElems / 2 : kColCtaElems;
-  if ((forced_p || (flags & CSAR_PLAN_COL_HALF_TILE)) && params) {
+  forced.e = (flags & CSAR_PLAN_COL_HALF_TILE) ? kColCtaElems / 2
+                                               : ((flags & CSAR_PLAN_COL_WIDE_TILE) ? 2 * kColCtaElems : kColCtaElems);
+  if ((forced_p || tile_flags) && params) {
     if (!forced_p) forced.p = col_conf_default(params->n_az).p;
     if (!col_conf_ok(params->n_az, forced))
       return fail(CSAR_E_UNSUPPORTED, "column configuration (cluster %d, %d values per CTA) not available "
@@ -908,7 +912,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->na = params->n_az;
   plan->nr = params->n_rg;
   plan->n = (int64_t)plan->na * plan->nr;
-  if (forced_p || (flags & CSAR_PLAN_COL_HALF_TILE)) {
+  if (forced_p || tile_flags) {
     plan->col = plan->col_res = forced;
   } else if (!tuned_conf(plan->na, plan->nr, &plan->col, &plan->col_res)) {
     plan->col = col_conf_default(plan->na);
@@ -1344,14 +1348,15 @@ csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* cho
     float main_ms, res_ms;
   };
   std::vector<Trial> trials;
-  for (int half = 0; half < 2; ++half) {
+  for (int size = 0; size < 3; ++size) {   // half, full and wide tiles
     for (int p = 1; p <= 16; p <<= 1) {
       ColConf c;
       c.p = p;
-      c.e = half ? kColCtaElems / 2 : kColCtaElems;
+      c.e = size == 0 ? kColCtaElems / 2 : (size == 1 ? kColCtaElems : 2 * kColCtaElems);
       if (!col_conf_ok(na, c)) continue;
       csar_plan plan = nullptr;
-      const uint32_t fl = CSAR_PLAN_COL_CLUSTER(p) | (half ? CSAR_PLAN_COL_HALF_TILE : 0u);
+      const uint32_t fl = CSAR_PLAN_COL_CLUSTER(p) |
+                          (size == 0 ? CSAR_PLAN_COL_HALF_TILE : (size == 2 ? CSAR_PLAN_COL_WIDE_TILE : 0u));
       if (csar_plan_create(params, fl, &plan) != CSAR_OK) continue;
       float pass[kPasses] = {};
       const bool ok = csar_solve(plan, y, m, x, &o, nullptr, nullptr) == CSAR_OK &&

@@ -205,17 +205,17 @@ def test_dense_iterate_groups_are_deterministic():
     (8192, 64, 2, 1), (8192, 64, 4, 1), (8192, 64, 8, 1), (8192, 64, 16, 1),
     (4096, 128, 1, 0), (4096, 128, 4, 0), (4096, 128, 8, 0), (4096, 128, 1, 1), (4096, 128, 2, 1),
     (4096, 128, 4, 1), (4096, 128, 8, 1), (2048, 128, 2, 0), (2048, 128, 4, 0), (2048, 128, 1, 1), (2048, 128, 4, 1),
-    (1024, 128, 1, 1)])
+    (1024, 128, 1, 1), (8192, 64, 4, 2), (8192, 64, 8, 2)])
 def test_every_column_configuration(na, nr, p, half):
     """The column passes under every configuration they are built for (cluster size,
-    full or half tiles: cross-CTA exchanges of the blocked and strided transforms, the
+    full, half (half = 1) or wide (half = 2) tiles: cross-CTA exchanges of the blocked and strided transforms, the
     residue pass, the selection and the sparse-input FFT path): 3 NIHT iterations on a
     2% scene against the oracle."""
     csar = lib()
     g, xt, y, mask = _problem(31, na, nr, frac=0.02)
     K = int(round(0.02 * na * nr))
     x_ref, st_ref = ita.ita(g, y, mask, K, 3, mu_mode="niht")
-    flags = csar.plan_col_cluster(p) | (csar.PLAN_COL_HALF_TILE if half else 0)
+    flags = csar.plan_col_cluster(p) | {0: 0, 1: csar.PLAN_COL_HALF_TILE, 2: csar.PLAN_COL_WIDE_TILE}[half]
     plan = csar.csar_plan_create(g, flags=flags)
     X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 3, mu_mode="niht", stats=True)
     csar.csar_plan_check(plan)
