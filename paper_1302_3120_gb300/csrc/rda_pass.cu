@@ -99,6 +99,58 @@ constexpr int rda_gamma_elems() { return kRdaChains<N> ? row_w(N) * regs_for(N) 
 // apart) fall on different banks.
 __device__ __forceinline__ int rda_pad(int i) { return i + (i >> 4); }
 
+// acc[pad(b + u mod N)] += w[u] x, u < 8.  Away from the row's end the 8 slots are
+// pad(b) + u, plus one from the first tap that crosses a pad slot on.
+template <int N>
+__device__ __forceinline__ void rda_scatter8(float2* acc, int b, float2 x, const float (&wt)[8]) {
+  const int bm = b & (N - 1);
+  if (bm <= N - 8) {
+    const int base = rda_pad(bm);
+    const int uc = 16 - (bm & 15);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float2* p = acc + base + u + (u >= uc ? 1 : 0);
+      float2 y = *p;
+      y.x = fmaf(x.x, wt[u], y.x);
+      y.y = fmaf(x.y, wt[u], y.y);
+      *p = y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float2* p = acc + rda_pad((b + u) & (N - 1));
+      float2 y = *p;
+      y.x = fmaf(x.x, wt[u], y.x);
+      y.y = fmaf(x.y, wt[u], y.y);
+      *p = y;
+    }
+  }
+}
+
+// sum_u w[u] row[b + u mod N], u < 8 (plain row).
+template <int N>
+__device__ __forceinline__ float2 rda_gather8(const float2* row, int b, const float (&wt)[8]) {
+  const int bm = b & (N - 1);
+  float2 y = make_float2(0.f, 0.f);
+  if (bm <= N - 8) {
+    const float2* p = row + bm;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float2 x = p[u];
+      y.x = fmaf(x.x, wt[u], y.x);
+      y.y = fmaf(x.y, wt[u], y.y);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float2 x = row[(b + u) & (N - 1)];
+      y.x = fmaf(x.x, wt[u], y.x);
+      y.y = fmaf(x.y, wt[u], y.y);
+    }
+  }
+  return y;
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   constexpr int WR = row_w(N);
@@ -147,7 +199,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
     phase_lin<R, 0, 16>(v, k.az, 16 * t - N / 2, 1);
     if constexpr (NJ > 1) phase_lin<R, 16, 32>(v, k.az, 16 * t, 1);
     for (int i = t; i < N + N / 16; i += QR) acc[i] = make_float2(0.f, 0.f);
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < NJ; ++j) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
@@ -157,15 +209,10 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
         const int b = rcmc_tap(k, tau, N, &f);
         float wt[8];
         rcmc_weights(f, wt);
-        const float2 x = v[16 * j + c];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float2* p = acc + rda_pad((b + u) & (N - 1));
-          float2 y = *p;
-          y.x = fmaf(x.x, wt[u], y.x);
-          y.y = fmaf(x.y, wt[u], y.y);
-          *p = y;
-        }
+        float2 x;
+        if constexpr (NJ == 1) x = v[c];
+        else x = j == 0 ? v[c] : v[16 + c];
+        rda_scatter8<N>(acc, b, x, wt);
       }
     }
     __syncthreads();
@@ -218,36 +265,38 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   }
   fft<N, true, L, false>(v, sm, tw, t, w);
   if constexpr (MODE == 0) {
-    // M: C then P_eta on the staged row
+    // M: C then P_eta on the staged row, one bin per step, stored as it is formed
+    // (P_eta as chains of 16 from two exact evaluations each, as in phase_lin)
     float2* rs = sm + w * N;
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < R; ++s) rs[t + s * QR] = cscale(v[s], a.scale);
     __syncthreads();
-#pragma unroll
+    float2 p = make_float2(1.f, 0.f), e1 = p, lam = p;
+#pragma unroll 4
     for (int s = 0; s < R; ++s) {
       const int tau = t + s * QR;
+      if ((s & 15) == 0) {
+        p = phase_eval(k.az, tau - N / 2, 1.f);
+        e1 = phase_eval(k.az, tau + QR - N / 2, 1.f);
+        lam = make_float2(fmaf(e1.x, p.x, e1.y * p.y), fmaf(e1.y, p.x, -e1.x * p.y));
+      } else {
+        p = (s & 15) == 1 ? e1 : cmul(p, lam);
+      }
       float f;
       const int b = rcmc_tap(k, tau, N, &f);
       float wt[8];
       rcmc_weights(f, wt);
-      float2 y = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float2 x = rs[(b + u) & (N - 1)];
-        y.x = fmaf(x.x, wt[u], y.x);
-        y.y = fmaf(x.y, wt[u], y.y);
-      }
-      v[s] = y;
+      const float2 y = rda_gather8<N>(rs, b, wt);
+      if (live) __stcs(&rp[tau], cmul(y, p));
     }
-    phase_lin<R, 0, R>(v, k.az, t - N / 2, QR);
   } else {
 #pragma unroll
     for (int s = 0; s < R; ++s) v[s] = cscale(v[s], a.scale);
-  }
-  if (live) {
+    if (live) {
 #pragma unroll
-    for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
+      for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
+    }
   }
 }
 
