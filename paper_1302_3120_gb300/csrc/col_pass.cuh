@@ -30,6 +30,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -81,9 +82,6 @@ __device__ __forceinline__ void cluster_barrier() {
 // release arrive (cluster scope) on the mbarrier of CTA k, and every thread waits on its
 // own mbarrier with acquire semantics.  Only P threads per CTA execute a cluster-scope
 // release, and loads issued before the wait are not held back by it.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ uint32_t cluster_map(uint32_t a, int rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
@@ -92,43 +90,8 @@ __device__ __forceinline__ uint32_t cluster_map(uint32_t a, int rank) {
 __device__ __forceinline__ void st_cluster(uint32_t a, float2 x) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x.x), "f"(x.y) : "memory");
 }
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for phase `parity` of the local mbarrier at `a`, for limit_ns at most; false if
-// the limit ran out (no endless spin).
-__device__ __forceinline__ bool mbar_wait_for(uint32_t a, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_test(a, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (;;) {
-    for (int k = 0; k < 64; ++k)
-      if (mbar_test(a, parity)) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-}
-// The exchange waits of the column passes: one second at most, after which a peer that
-// never signalled makes the kernel latch kErrTimeout and go on.
-__device__ __forceinline__ void mbar_wait(uint32_t a, uint32_t parity, Ctl* ctl) {
-  if (!mbar_wait_for(a, parity, 1000000000ull) && ctl) atomicOr(&ctl->err, kErrTimeout);
 }
 // Signal on mbarrier `mb` (local address; the same offset in every CTA) of all P CTAs
 // that this CTA's prior shared-memory work (remote stores, or reads of its own buffer)

@@ -10,12 +10,15 @@
 // with the conjugates (H3*, H2*, H1*) it is the middle of G (Section III-C/D).
 // In the ITA's range pass of M the pass first forms its input F_a r = F_a(S.Y) -
 // F_a(S.G(X)) from the echo's azimuth transform and the residue column pass's output,
-// with the partial sums of |F_a r|^2.
+// with the partial sums of |F_a r|^2; the CTA's rows of F_a(S.Y) arrive by one bulk
+// asynchronous copy into the (still unused) exchange buffer while the threads load
+// the other operand, so the two reads overlap.
 // j' = j - N_r/2 is the signed range-time bin, m the signed range-frequency bin;
 // each phase is evaluated on the fly from per-row FP64-derived coefficients
 // (phase.cuh), so the pass reads and writes each element exactly once.
 #include "fft.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace csar {
 
@@ -35,11 +38,20 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   if (a.gate && *a.gate != a.gate_val) return;
   float2* sm = smem;
   float2* tw = smem + L::kSmemElems;
-  float2* gam = tw + kTwLo + kTwHi + 16;   // after 32 floats of reduction scratch
-  load_twiddles(tw, a.tw);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + kTwLo + kTwHi + 16);   // after 32 floats of reduction scratch
+  float2* gam = tw + kTwLo + kTwHi + 18;
   const int tid = threadIdx.x;
+  const int row0 = blockIdx.x * WR;
+  if (a.yf && tid == 0) {
+    // rows row0 .. row0 + live_rows - 1 of F_a(S.Y) into the exchange buffer, plain order
+    const int live_rows = a.n_rows - row0 < WR ? a.n_rows - row0 : WR;
+    const uint32_t mb = smem_addr(mbar);
+    mbar_init(mb, 1u);
+    bulk_load_armed(smem_addr(sm), a.yf + (size_t)row0 * N, (uint32_t)(live_rows * N * sizeof(float2)), mb);
+  }
+  load_twiddles(tw, a.tw);
   const int w = tid / QR, t = tid % QR;
-  const int row = blockIdx.x * WR + w;
+  const int row = row0 + w;
   const bool live = row < a.n_rows;
   const RowCoef* cp = a.coef + (live ? row : 0);
   float2* rp = a.data + (size_t)(live ? row : 0) * N;
@@ -60,21 +72,23 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   const float2* gw = gam + w * 3 * R;
   if (a.yf) {
     // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
-    const float2* yp = a.yf + (size_t)(live ? row : 0) * N;
+    if constexpr (!kRowChains<N>) __syncthreads();   // the mbarrier is initialised
+    const uint32_t mb = smem_addr(mbar);
+    if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
+      // the copy did not land within a second: report it, and give it one more second
+      // before the buffer is reused
+      atomicOr(&a.ctl->err, kErrTimeout);
+      mbar_wait_for(mb, 0u, 1000000000ull);
+    }
+    const float2* ys = sm + w * N;
     float acc = 0.f;
     bool bad = false;
-    constexpr int kG = R >= 8 ? 8 : R;   // loads in flight per group (register pressure)
 #pragma unroll
-    for (int g0 = 0; g0 < R; g0 += kG) {
-      float2 y[kG];
-#pragma unroll
-      for (int j = 0; j < kG; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kG; ++j) {
-        v[g0 + j] = csub(y[j], v[g0 + j]);
-        acc += cabs2(v[g0 + j]);
-        bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
-      }
+    for (int s = 0; s < R; ++s) {
+      const float2 y = live ? ys[t + s * QR] : make_float2(0.f, 0.f);
+      v[s] = csub(y, v[s]);
+      acc += cabs2(v[s]);
+      bad |= !(isfinite(v[s].x) && isfinite(v[s].y));
     }
     if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
 #pragma unroll
@@ -124,7 +138,8 @@ template <int N>
 static size_t row_smem() {
   using L = Layout<N, row_w(N), false>;
   return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
-         32 * sizeof(float) + (kRowChains<N> ? (size_t)row_w(N) * 3 * regs_for(N) * sizeof(float2) : 0);
+         32 * sizeof(float) + 2 * sizeof(float2) +
+         (kRowChains<N> ? (size_t)row_w(N) * 3 * regs_for(N) * sizeof(float2) : 0);
 }
 
 #define CSAR_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
