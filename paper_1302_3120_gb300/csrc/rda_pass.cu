@@ -38,8 +38,12 @@ __device__ __forceinline__ int rcmc_tap(const RcmcCoef& k, int tau, int nr, floa
   const float n1 = rintf(k.a0_hi), n2 = rintf(p);
   const float fr = (k.a0_hi - n1) + (p - n2) + (k.a0_lo + e + k.al_lo * fj);
   const float fl = floorf(fr);
-  *f = fr - fl;
-  return tau + (int)n1 + (int)n2 + (int)fl - 3;
+  const float fc = fr - fl;
+  // a fraction a few 1e-8 under 1 (fr just below an integer) rounds to 1: that is the
+  // next tap with fraction 0
+  const bool up = fc >= 1.f;
+  *f = up ? 0.f : fc;
+  return tau + (int)n1 + (int)n2 + (int)fl - 3 + (up ? 1 : 0);
 }
 
 // Weights w[t] = sinc(m - f), m = t - 3, from one sinpi (sin(pi (m - f)) =
@@ -47,7 +51,7 @@ __device__ __forceinline__ int rcmc_tap(const RcmcCoef& k, int tau, int nr, floa
 // reciprocal of their product (batch inversion: prefix products forward, the inverse
 // carried back), a few ulp each.
 __device__ __forceinline__ void rcmc_weights(float f, float (&w)[8]) {
-  if (f <= 0.f) {
+  if (!(f > 1e-20f)) {      // f = 0 (and fractions too small to matter): the tap itself
 #pragma unroll
     for (int t = 0; t < 8; ++t) w[t] = t == 3 ? 1.f : 0.f;
     return;

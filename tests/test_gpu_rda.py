@@ -174,3 +174,30 @@ def test_rda_G_is_deterministic():
         a = csar.csar_G(plan, x)
         b = csar.csar_G(plan, x)
         assert torch.equal(a, b)
+
+
+def test_rda_full_size_spaceborne_properties():
+    """At the 8192 x 8192 spaceborne size of the operator benchmark (same launch
+    configuration), properties that hold at any size: Theorem 1 (<G x, y> = <x, M y>,
+    FP64 sums of the GPU outputs), and a point target's exact echo (the GPU simulator,
+    itself parity-tested against the oracle) focused by M on the target's pixel."""
+    import torch
+    csar = lib()
+    g = synth.spaceborne(8192, 8192)
+    plan = csar.csar_plan_create(g, flags=csar.PLAN_RDA)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randn((8192, 8192), dtype=torch.complex64, device="cuda", generator=gen)
+    y = torch.randn((8192, 8192), dtype=torch.complex64, device="cuda", generator=gen)
+    gx = csar.csar_G(plan, x)
+    my = csar.csar_M(plan, y)
+    assert torch.isfinite(torch.view_as_real(gx)).all().item()
+    assert torch.isfinite(torch.view_as_real(my)).all().item()
+    lhs = torch.vdot(y.reshape(-1).to(torch.complex128), gx.reshape(-1).to(torch.complex128))
+    rhs = torch.vdot(my.reshape(-1).to(torch.complex128), x.reshape(-1).to(torch.complex128))
+    assert abs((lhs - rhs) / lhs).item() < 1e-5
+    del x, y, gx, my
+    # a point target's echo (exact model, GPU simulator) focuses on its pixel
+    s = csar.csar_echo_points(g, [4096], [4096], [1.0])
+    img = csar.csar_M(plan, s)
+    pk = int(torch.argmax(img.abs()).item())
+    assert divmod(pk, 8192) == (4096, 4096)
