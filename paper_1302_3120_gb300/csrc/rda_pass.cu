@@ -18,8 +18,9 @@
 // The transpose scatters without atomics: the first tap b(tau) rises by at least one
 // per bin (slope 1 + alpha, alpha >= 0), so bins 16 apart write disjoint 8-bin spans.
 // Thread t holds the bins 16 t + c + j N_r / 2 (c < 16); the rounds (c, j) each
-// update, in plain read-add-writes, one bin per thread, with a barrier between rounds
-// (within a half row the spans cannot wrap onto each other while alpha < 1 - 18/N_r).
+// update, in plain read-add-writes, one bin per thread; threads may drift up to 7
+// rounds apart (a barrier every 8 rounds) without their spans meeting, and within a
+// half row the spans cannot wrap onto each other while alpha < 1 - 18/N_r.
 // Every accumulator therefore sums its terms in the fixed order of the rounds and G is
 // deterministic.
 // The migration dr = alpha (c0 + j') (alpha = 1/D - 1, c0 = 2 R_ref fs / c,
@@ -207,7 +208,10 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
     for (int j = 0; j < NJ; ++j) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        __syncthreads();
+        // threads t < t' at rounds c, c' with |c - c'| <= 7 hold bins at least 9 apart,
+        // whose first taps differ by at least 8: disjoint spans.  A barrier every 8
+        // rounds keeps every thread within 7 rounds of the others.
+        if ((c & 7) == 0) __syncthreads();
         const int tau = 16 * t + c + j * (N / 2);
         float f;
         const int b = rcmc_tap(k, tau, N, &f);
