@@ -105,31 +105,31 @@ constexpr int rda_gamma_elems() { return kRdaChains<N> ? row_w(N) * regs_for(N) 
 __device__ __forceinline__ int rda_pad(int i) { return i + (i >> 4); }
 
 // acc[pad(b + u mod N)] += w[u] x, u < 8.  Away from the row's end the 8 slots are
-// pad(b) + u, plus one from the first tap that crosses a pad slot on.
+// pad(b) + u, plus one from the first tap that crosses a pad slot on.  The 8 slots are
+// distinct: all are read before any is written, so the reads overlap.
 template <int N>
 __device__ __forceinline__ void rda_scatter8(float2* acc, int b, float2 x, const float (&wt)[8]) {
   const int bm = b & (N - 1);
+  int ad[8];
   if (bm <= N - 8) {
     const int base = rda_pad(bm);
     const int uc = 16 - (bm & 15);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      float2* p = acc + base + u + (u >= uc ? 1 : 0);
-      float2 y = *p;
-      y.x = fmaf(x.x, wt[u], y.x);
-      y.y = fmaf(x.y, wt[u], y.y);
-      *p = y;
-    }
+    for (int u = 0; u < 8; ++u) ad[u] = base + u + (u >= uc ? 1 : 0);
   } else {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      float2* p = acc + rda_pad((b + u) & (N - 1));
-      float2 y = *p;
-      y.x = fmaf(x.x, wt[u], y.x);
-      y.y = fmaf(x.y, wt[u], y.y);
-      *p = y;
-    }
+    for (int u = 0; u < 8; ++u) ad[u] = rda_pad((b + u) & (N - 1));
   }
+  float2 y[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) y[u] = acc[ad[u]];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    y[u].x = fmaf(x.x, wt[u], y[u].x);
+    y[u].y = fmaf(x.y, wt[u], y[u].y);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[ad[u]] = y[u];
 }
 
 // sum_u w[u] row[b + u mod N], u < 8 (plain row).
