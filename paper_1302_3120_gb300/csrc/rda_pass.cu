@@ -9,7 +9,7 @@
 // and each operator is a column FFT, this row pass, a column IFFT (three passes, like
 // the chirp-scaling pair).  In the ITA the pass of M also takes the residue form of
 // the chirp-scaling range pass (F_a r = F_a(S.Y) - input, with the partial sums of
-// |F_a r|^2).  Per azimuth-frequency row, in registers and shared memory:
+// |F_a r|^2; F_a(S.Y) by a bulk asynchronous copy overlapping the other load).  Per azimuth-frequency row, in registers and shared memory:
 //   M:  range FFT, x P_tau, range IFFT / N_r, row staged in shared memory, every bin
 //       tau interpolated from bins b..b+7 (b = floor(tau + dr) - 3, mod N_r) with
 //       weights sinc(b + t - tau - dr), x P_eta(tau);
@@ -28,6 +28,7 @@
 // fraction, which sets the weights, is accurate to ~1e-7 samples.
 #include "fft.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace csar {
 
@@ -169,9 +170,19 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   float2* sm = smem;                         // transform exchanges, and the staged rows
   float2* tw = smem + L::kSmemElems;
   float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);   // 32 floats
-  float2* gam = tw + kTwLo + kTwHi + 16;      // Gamma tables of the range filter, per row
-  load_twiddles(tw, a.tw);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + kTwLo + kTwHi + 16);
+  float2* gam = tw + kTwLo + kTwHi + 18;      // Gamma tables of the range filter, per row
   const int tid = threadIdx.x;
+  if (MODE == 0 && a.yf && tid == 0) {
+    // residue form: this CTA's rows of F_a(S.Y) by one bulk asynchronous copy into the
+    // still unused exchange buffer, while the threads load the other operand
+    const int row0 = blockIdx.x * WR;
+    const int live_rows = a.n_rows - row0 < WR ? a.n_rows - row0 : WR;
+    const uint32_t mb = smem_addr(mbar);
+    mbar_init(mb, 1u);
+    bulk_load_armed(smem_addr(sm), a.yf + (size_t)row0 * N, (uint32_t)(live_rows * N * sizeof(float2)), mb);
+  }
+  load_twiddles(tw, a.tw);
   const int w = tid / QR, t = tid % QR;
   const int row = blockIdx.x * WR + w;
   const bool live = row < a.n_rows;
@@ -231,20 +242,23 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
     for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&rp[t + s * QR]) : make_float2(0.f, 0.f);
     if (a.yf) {
       // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
-      const float2* yp = a.yf + (size_t)rw * N;
+      __syncthreads();   // the mbarrier is initialised
+      const uint32_t mb = smem_addr(mbar);
+      if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
+        // the copy did not land within a second: report it, and give it one more second
+        // before the buffer is reused
+        atomicOr(&a.ctl->err, kErrTimeout);
+        mbar_wait_for(mb, 0u, 1000000000ull);
+      }
+      const float2* ys = sm + w * N;
       float sq = 0.f;
       bool bad = false;
 #pragma unroll
-      for (int g0 = 0; g0 < R; g0 += 8) {
-        float2 y[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          v[g0 + j] = csub(y[j], v[g0 + j]);
-          sq += cabs2(v[g0 + j]);
-          bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
-        }
+      for (int s = 0; s < R; ++s) {
+        const float2 y = live ? ys[t + s * QR] : make_float2(0.f, 0.f);
+        v[s] = csub(y, v[s]);
+        sq += cabs2(v[s]);
+        bad |= !(isfinite(v[s].x) && isfinite(v[s].y));
       }
       if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
 #pragma unroll
@@ -311,7 +325,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
 template <int N>
 static size_t rda_smem() {
   using L = Layout<N, row_w(N), false>;
-  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi + 16) * sizeof(float2) +
+  return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi + 18) * sizeof(float2) +
          (size_t)rda_gamma_elems<N>() * sizeof(float2);
 }
 
