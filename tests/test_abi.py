@@ -56,3 +56,33 @@ def test_invalid_arguments_rejected_on_host():
     assert csar.lib.csar_plan_create(ctypes.byref(p), 7, ctypes.byref(h)) == 1
     assert h.value is None
     assert csar.lib.csar_plan_create(None, 0, ctypes.byref(h)) == 1
+
+
+def test_echo_simulator_and_tile_flags_rejected_on_host():
+    """Host-side validation of the echo simulator and of the plan's column-tile flags
+    (no CUDA call is reached)."""
+    import dataclasses
+    import numpy as np
+    import synth
+    from paper_1302_3120_gb300 import csar
+    g = synth.airborne(64, 64)
+    p = csar.params_of(g)
+    rows = np.array([64], np.int32)          # off the grid
+    cols = np.array([0], np.int32)
+    amp = np.array([1.0, 0.0], np.float32)
+    fake = ctypes.c_void_p(16)               # never dereferenced: validation fails first
+    st = csar.lib.csar_echo_points(ctypes.byref(p), rows.ctypes.data, cols.ctypes.data,
+                                   amp.ctypes.data, 1, fake, 0, None)
+    assert st == 1 and "off the grid" in csar.lib.csar_last_error().decode()
+    p0 = csar.params_of(dataclasses.replace(g, antenna_len=0.0))
+    rows[0] = 10
+    st = csar.lib.csar_echo_points(ctypes.byref(p0), rows.ctypes.data, cols.ctypes.data,
+                                   amp.ctypes.data, 1, fake, 0, None)
+    assert st == 1 and "antenna_len" in csar.lib.csar_last_error().decode()
+    st = csar.lib.csar_echo_points(ctypes.byref(p), rows.ctypes.data, cols.ctypes.data,
+                                   amp.ctypes.data, -1, fake, 0, None)
+    assert st == 1
+    h = ctypes.c_void_p()
+    both = csar.PLAN_COL_HALF_TILE | csar.PLAN_COL_WIDE_TILE
+    assert csar.lib.csar_plan_create(ctypes.byref(p), both, ctypes.byref(h)) == 2
+    assert h.value is None
