@@ -9,14 +9,16 @@
 // and each operator is a column FFT, this row pass, a column IFFT (three passes, like
 // the chirp-scaling pair).  In the ITA the pass of M also takes the residue form of
 // the chirp-scaling range pass (F_a r = F_a(S.Y) - input, with the partial sums of
-// |F_a r|^2; F_a(S.Y) by a bulk asynchronous copy overlapping the other load).  Per azimuth-frequency row, in registers and shared memory:
+// |F_a r|^2; F_a(S.Y) by a bulk asynchronous copy overlapping the other load).
+// Per azimuth-frequency row, in registers and shared memory:
 //   M:  range FFT, x P_tau, range IFFT / N_r, row staged in shared memory, every bin
 //       tau interpolated from bins b..b+7 (b = floor(tau + dr) - 3, mod N_r) with
 //       weights sinc(b + t - tau - dr), x P_eta(tau);
 //   G:  x conj(P_eta), each bin added with the same weights onto the bins it is read
 //       from in M (D = C^T), range FFT, x conj(P_tau), range IFFT / N_r.
-// The transpose scatters without atomics: the first tap b(tau) rises by at least one
-// per bin (slope 1 + alpha, alpha >= 0), so bins 16 apart write disjoint 8-bin spans.
+// The transpose scatters without atomics: the first tap b(tau) rises by one per bin up
+// to a rounding step (slope 1 + alpha, alpha >= 0), so bins 9 or more apart start
+// 8-bin spans at least 8 apart, which are disjoint.
 // Thread t holds the bins 16 t + c + j N_r / 2 (c < 16); the rounds (c, j) each
 // update, in plain read-add-writes, one bin per thread; threads may drift up to 7
 // rounds apart (a barrier every 8 rounds) without their spans meeting, and within a
