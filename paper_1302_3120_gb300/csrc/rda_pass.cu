@@ -76,25 +76,6 @@ __device__ __forceinline__ void rcmc_weights(float f, float (&w)[8]) {
   w[0] = inv;
 }
 
-// v[s] *= exp(j 2 pi (A + B (i0 + (s - S0) d))) for s in [S0, S1): a linear phase as
-// chains of 16 from two exact evaluations each.
-template <int R, int S0, int S1>
-__device__ __forceinline__ void phase_lin(float2 (&v)[R], const PhaseCoef& c, int i0, int d) {
-#pragma unroll
-  for (int b = S0; b < S1; b += 16) {
-    const int ib = i0 + (b - S0) * d;
-    float2 p = phase_eval(c, ib, 1.f);
-    const float2 e1 = phase_eval(c, ib + d, 1.f);
-    const float2 lam = make_float2(fmaf(e1.x, p.x, e1.y * p.y), fmaf(e1.y, p.x, -e1.x * p.y));
-    v[b] = cmul(v[b], p);
-#pragma unroll
-    for (int u = 1; u < 16 && b + u < S1; ++u) {
-      p = u == 1 ? e1 : cmul(p, lam);
-      v[b + u] = cmul(v[b + u], p);
-    }
-  }
-}
-
 // Rows of at least 1024 bins apply the range filter as chains with per-row Gamma tables
 // in shared memory; shorter rows use the re-anchored recurrence.
 template <int N>
@@ -201,38 +182,32 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   const float2* gw = gam + w * R;
   float2 v[R];
   if constexpr (MODE == 1) {
-    // G: bins 16 t + c + j N/2 in v[16 j + c]; conj(P_eta) (coefficients of G's rows)
+    // G: thread t takes bins 16 t + c + j N/2 (c < 16) one per round, reading each from
+    // global memory as it goes (the row's lines stay in L1 across the 16 rounds), times
+    // conj(P_eta) (coefficients of G's rows) as chains of 16 from two exact evaluations
     constexpr int NJ = R / 16;
     float2* acc = sm + w * (N + N / 16);
-#pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      const float4* src = reinterpret_cast<const float4*>(rp + 16 * t + j * (N / 2));
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const float4 q = live ? __ldcs(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[16 * j + 2 * c] = make_float2(q.x, q.y);
-        v[16 * j + 2 * c + 1] = make_float2(q.z, q.w);
-      }
-    }
-    phase_lin<R, 0, 16>(v, k.az, 16 * t - N / 2, 1);
-    if constexpr (NJ > 1) phase_lin<R, 16, 32>(v, k.az, 16 * t, 1);
     for (int i = t; i < N + N / 16; i += QR) acc[i] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int j = 0; j < NJ; ++j) {
-#pragma unroll
+      const int tau0 = 16 * t + j * (N / 2);
+      float2 p = phase_eval(k.az, tau0 - N / 2, 1.f);
+      const float2 e1 = phase_eval(k.az, tau0 + 1 - N / 2, 1.f);
+      const float2 lam = make_float2(fmaf(e1.x, p.x, e1.y * p.y), fmaf(e1.y, p.x, -e1.x * p.y));
+#pragma unroll 1
       for (int c = 0; c < 16; ++c) {
         // threads t < t' at rounds c, c' with |c - c'| <= 7 hold bins at least 9 apart,
         // whose first taps differ by at least 8: disjoint spans.  A barrier every 8
         // rounds keeps every thread within 7 rounds of the others.
         if ((c & 7) == 0) __syncthreads();
-        const int tau = 16 * t + c + j * (N / 2);
+        const int tau = tau0 + c;
+        if (c == 1) p = e1;
+        else if (c > 1) p = cmul(p, lam);
+        const float2 x = live ? cmul(__ldg(&rp[tau]), p) : make_float2(0.f, 0.f);
         float f;
         const int b = rcmc_tap(k, tau, N, &f);
         float wt[8];
         rcmc_weights(f, wt);
-        float2 x;
-        if constexpr (NJ == 1) x = v[c];
-        else x = j == 0 ? v[c] : v[16 + c];
         rda_scatter8<N>(acc, b, x, wt);
       }
     }
@@ -290,7 +265,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   fft<N, true, L, false>(v, sm, tw, t, w);
   if constexpr (MODE == 0) {
     // M: C then P_eta on the staged row, one bin per step, stored as it is formed
-    // (P_eta as chains of 16 from two exact evaluations each, as in phase_lin)
+    // (P_eta, a linear phase, as chains of 16 from two exact evaluations each)
     float2* rs = sm + w * N;
     __syncthreads();
 #pragma unroll
