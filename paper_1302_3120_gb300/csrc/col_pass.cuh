@@ -1,10 +1,11 @@
 // col_pass.cuh — azimuth (column, strided-axis) passes.
 //
 // A column transform of length N_a is split over a thread-block cluster of P CTAs
-// (P = 4 at N_a = 8192, 2 at 4096, else 1), each on its own SM, that together own a
-// tile of W >= 4 adjacent columns (32-byte row segments, full DRAM sectors).  With
-// N_a = P * Q, each CTA keeps Q*W <= 8192 complex64 values (64 KiB) in registers,
-// so two CTAs fit per SM and one CTA's loads overlap the other's arithmetic.
+// (P = 4 at N_a = 8192, 2 at 4096, else 1 by default), that together own a tile of
+// W >= 4 adjacent columns (32-byte row segments, full DRAM sectors).  With N_a = P * Q,
+// each CTA keeps E = Q*W complex64 values in registers: 8192 (64 KiB, two CTAs per SM,
+// so one CTA's loads overlap the other's arithmetic), 4096 (four per SM) or 16384 (one
+// per SM, 8- or 16-column tiles).
 //
 // Forward/inverse transform "BS" (blocked rows in, strided rows out):
 //   CTA c loads rows Q*n1 + n2 for its block of n2 (all n1), does the length-P DFT

@@ -167,7 +167,7 @@ struct RdaArgs {
 
 // Column passes: a cluster of P CTAs owns col_w(N, P, E) adjacent columns; each CTA
 // holds E = N*W/P complex64 values (E = 8192: 64 KiB and two CTAs per SM; E = 4096:
-// 32 KiB and four CTAs per SM).  A column configuration (P, E) is a plan choice among
+// 32 KiB and four CTAs per SM; E = 16384: 128 KiB and one CTA of 1024 threads per SM).  A column configuration (P, E) is a plan choice among
 // col_conf_ok(N, conf) (see col_dispatch.cu).
 constexpr int kColCtaElems = 8192;   // default complex64 values per column-pass CTA
 struct ColConf {
