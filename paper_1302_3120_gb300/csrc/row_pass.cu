@@ -28,7 +28,9 @@ namespace csar {
 template <int N>
 constexpr bool kRowChains = N >= 1024;
 
-template <int N>
+// RESID: the residue form (a.yf set), a separate instance so that the plain pass
+// carries none of its code.
+template <int N, bool RESID>
 __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   constexpr int WR = row_w(N);
   constexpr int R = regs_for(N);
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   float2* gam = tw + kTwLo + kTwHi + 18;
   const int tid = threadIdx.x;
   const int row0 = blockIdx.x * WR;
-  if (a.yf && tid == 0) {
+  if (RESID && tid == 0) {
     // rows row0 .. row0 + live_rows - 1 of F_a(S.Y) into the exchange buffer, plain order
     const int live_rows = a.n_rows - row0 < WR ? a.n_rows - row0 : WR;
     const uint32_t mb = smem_addr(mbar);
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
     __syncthreads();
   }
   const float2* gw = gam + w * 3 * R;
-  if (a.yf) {
+  if constexpr (RESID) {
     // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
     if constexpr (!kRowChains<N>) __syncthreads();   // the mbarrier is initialised
     const uint32_t mb = smem_addr(mbar);
@@ -146,10 +148,16 @@ static size_t row_smem() {
 
 cudaError_t row_set_attributes(int nr) {
   switch (nr) {
-#define CSAR_CASE(N)                                                                     \
-  case N:                                                                                \
-    return cudaFuncSetAttribute(k_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                (int)row_smem<N>());
+#define CSAR_CASE(N)                                                                         \
+  case N: {                                                                                  \
+    cudaError_t e = cudaFuncSetAttribute(k_row<N, false>,                                    \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                         (int)row_smem<N>());                                \
+    if (e == cudaSuccess)                                                                    \
+      e = cudaFuncSetAttribute(k_row<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                               (int)row_smem<N>());                                          \
+    return e;                                                                                \
+  }
     CSAR_ROW_SIZES(CSAR_CASE)
 #undef CSAR_CASE
     default: return cudaErrorInvalidValue;
@@ -161,7 +169,8 @@ cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s) {
 #define CSAR_CASE(N)                                                              \
   case N: {                                                                       \
     const int grid = (a.n_rows + row_w(N) - 1) / row_w(N);                        \
-    k_row<N><<<grid, row_threads(N), row_smem<N>(), s>>>(a);                      \
+    if (a.yf) k_row<N, true><<<grid, row_threads(N), row_smem<N>(), s>>>(a);      \
+    else k_row<N, false><<<grid, row_threads(N), row_smem<N>(), s>>>(a);          \
     return cudaGetLastError();                                                    \
   }
     CSAR_ROW_SIZES(CSAR_CASE)
