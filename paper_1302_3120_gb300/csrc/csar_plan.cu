@@ -904,6 +904,15 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   if (csar_status st = validate(params)) return st;
   std::vector<RowCoef> cg(params->n_az), cm(params->n_az);
   if (csar_status st = build_coefs_into(*params, cg.data(), cm.data())) return st;
+  // range-Doppler tables, also checked on the host before any CUDA call
+  std::vector<RowCoef> rg, rm;
+  std::vector<RcmcCoef> rc;
+  if (flags & CSAR_PLAN_RDA) {
+    rg.resize(params->n_az);
+    rm.resize(params->n_az);
+    rc.resize(2 * (size_t)params->n_az);
+    if (csar_status st = build_rda_coefs(*params, rg.data(), rm.data(), rc.data())) return st;
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   csar_plan plan = new csar_plan_s();
@@ -945,9 +954,6 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(cudaMemcpy(plan->coef_g, cg.data(), cg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
   PK(cudaMemcpy(plan->coef_m, cm.data(), cm.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));
   if (flags & CSAR_PLAN_RDA) {
-    std::vector<RowCoef> rg(params->n_az), rm(params->n_az);
-    std::vector<RcmcCoef> rc(2 * (size_t)params->n_az);
-    if (csar_status st = build_rda_coefs(*params, rg.data(), rm.data(), rc.data())) return bail(st);
     PK(rda_set_attributes(plan->nr));
     PK(dalloc(&plan->rda_rg_g, plan->na));
     PK(dalloc(&plan->rda_rg_m, plan->na));

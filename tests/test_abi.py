@@ -86,3 +86,20 @@ def test_echo_simulator_and_tile_flags_rejected_on_host():
     both = csar.PLAN_COL_HALF_TILE | csar.PLAN_COL_WIDE_TILE
     assert csar.lib.csar_plan_create(ctypes.byref(p), both, ctypes.byref(h)) == 2
     assert h.value is None
+
+
+def test_rda_plan_checks_on_host():
+    """A range-Doppler plan's tables are checked before any CUDA call: a migration
+    slope above 1/2 (edge Doppler at 0.8 of 2V/lambda) or a Doppler beyond 2V/lambda is
+    refused (CSAR_E_UNSUPPORTED) without a GPU."""
+    import dataclasses
+    import synth
+    from paper_1302_3120_gb300 import csar
+    for frac in (0.8, 1.2):
+        g = dataclasses.replace(synth.airborne(64, 64), prf=frac * 4 * 150.0 / 0.03)
+        p = csar.params_of(g)
+        h = ctypes.c_void_p()
+        assert csar.lib.csar_plan_create(ctypes.byref(p), csar.PLAN_RDA, ctypes.byref(h)) == 2
+        assert h.value is None
+        msg = csar.lib.csar_last_error().decode()
+        assert ("slope" in msg) or ("Doppler" in msg) or ("phase" in msg), msg
