@@ -10,9 +10,9 @@
 // with the conjugates (H3*, H2*, H1*) it is the middle of G (Section III-C/D).
 // In the ITA's range pass of M the pass first forms its input F_a r = F_a(S.Y) -
 // F_a(S.G(X)) from the echo's azimuth transform and the residue column pass's output,
-// with the partial sums of |F_a r|^2; the CTA's rows of F_a(S.Y) arrive by one bulk
-// asynchronous copy into the (still unused) exchange buffer while the threads load
-// the other operand, so the two reads overlap.
+// with the partial sums of |F_a r|^2; at N_r = 8192 the CTA's row of F_a(S.Y) arrives
+// by one bulk asynchronous copy into the (still unused) exchange buffer while the
+// threads load the other operand, so the two reads overlap.
 // j' = j - N_r/2 is the signed range-time bin, m the signed range-frequency bin;
 // each phase is evaluated on the fly from per-row FP64-derived coefficients
 // (phase.cuh), so the pass reads and writes each element exactly once.
@@ -27,6 +27,12 @@ namespace csar {
 // rows per CTA, keep the re-anchored recurrence (phase_ap).
 template <int N>
 constexpr bool kRowChains = N >= 1024;
+
+// The residue form takes F_a(S.Y) by one bulk asynchronous copy at N_r = 8192 (one row
+// per CTA); shorter rows load it in groups of 8 per thread, which keeps their register
+// allocation free of spills.
+template <int N>
+constexpr bool kBulkY = N == 8192;
 
 // RESID: the residue form (a.yf set), a separate instance so that the plain pass
 // carries none of its code.
@@ -44,7 +50,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   float2* gam = tw + kTwLo + kTwHi + 18;
   const int tid = threadIdx.x;
   const int row0 = blockIdx.x * WR;
-  if (RESID && tid == 0) {
+  if (RESID && kBulkY<N> && tid == 0) {
     // rows row0 .. row0 + live_rows - 1 of F_a(S.Y) into the exchange buffer, plain order
     const int live_rows = a.n_rows - row0 < WR ? a.n_rows - row0 : WR;
     const uint32_t mb = smem_addr(mbar);
@@ -74,23 +80,39 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   const float2* gw = gam + w * 3 * R;
   if constexpr (RESID) {
     // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
-    if constexpr (!kRowChains<N>) __syncthreads();   // the mbarrier is initialised
-    const uint32_t mb = smem_addr(mbar);
-    if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
-      // the copy did not land within a second: report it, and give it one more second
-      // before the buffer is reused
-      atomicOr(&a.ctl->err, kErrTimeout);
-      mbar_wait_for(mb, 0u, 1000000000ull);
-    }
-    const float2* ys = sm + w * N;
     float acc = 0.f;
     bool bad = false;
+    if constexpr (kBulkY<N>) {
+      const uint32_t mb = smem_addr(mbar);   // initialised before the Gamma-table barrier
+      if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
+        // the copy did not land within a second: report it, and give it one more second
+        // before the buffer is reused
+        atomicOr(&a.ctl->err, kErrTimeout);
+        mbar_wait_for(mb, 0u, 1000000000ull);
+      }
+      const float2* ys = sm + w * N;
 #pragma unroll
-    for (int s = 0; s < R; ++s) {
-      const float2 y = live ? ys[t + s * QR] : make_float2(0.f, 0.f);
-      v[s] = csub(y, v[s]);
-      acc += cabs2(v[s]);
-      bad |= !(isfinite(v[s].x) && isfinite(v[s].y));
+      for (int s = 0; s < R; ++s) {
+        const float2 y = live ? ys[t + s * QR] : make_float2(0.f, 0.f);
+        v[s] = csub(y, v[s]);
+        acc += cabs2(v[s]);
+        bad |= !(isfinite(v[s].x) && isfinite(v[s].y));
+      }
+    } else {
+      const float2* yp = a.yf + (size_t)(live ? row : 0) * N;
+      constexpr int kG = R >= 8 ? 8 : R;   // loads in flight per group (register pressure)
+#pragma unroll
+      for (int g0 = 0; g0 < R; g0 += kG) {
+        float2 y[kG];
+#pragma unroll
+        for (int j = 0; j < kG; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kG; ++j) {
+          v[g0 + j] = csub(y[j], v[g0 + j]);
+          acc += cabs2(v[g0 + j]);
+          bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
+        }
+      }
     }
     if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
 #pragma unroll
