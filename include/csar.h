@@ -127,7 +127,7 @@ typedef struct {
  * the chirp-scaling functions H1 (chirp scaling), H2 (range compression, SRC and
  * bulk RCMC) and H3 (azimuth matched filter and residual phase) and uploads them,
  * and allocates the plan's device workspace.  `flags`: 0 (the autotuned or default
- * column configuration) or the CSAR_PLAN_COL_* flags above.  The plan uses the
+ * column configuration), the CSAR_PLAN_COL_* flags above, and CSAR_PLAN_RDA.  The plan uses the
  * current CUDA device.  On error *out is set to NULL.  CSAR_E_UNSUPPORTED if the
  * geometry's phase arguments exceed what the on-the-fly phase evaluation covers
  * (|range-linear term| >= 2^22 cycles). */
@@ -138,13 +138,16 @@ csar_status csar_plan_destroy(csar_plan plan);
 
 /* y_dev = G(x_dev): the approximated observation (Section III-C/D, Eq. (18) with
  * chirp-scaling sub-operations): azimuth FFT, x conj(H3), range FFT, x conj(H2),
- * range IFFT, x conj(H1), azimuth IFFT.  x_dev, y_dev: n_az*n_rg complex64 device
- * arrays; x_dev == y_dev (in place) is allowed; otherwise they must not overlap. */
+ * range IFFT, x conj(H1), azimuth IFFT (on a CSAR_PLAN_RDA plan: azimuth FFT,
+ * x conj(P_eta), D = C^T, range compression with the conjugate filter, azimuth IFFT).
+ * x_dev, y_dev: n_az*n_rg complex64 device arrays; x_dev == y_dev (in place) is
+ * allowed; otherwise they must not overlap. */
 csar_status csar_G(csar_plan plan, const void* x_dev, void* y_dev, void* stream);
 
 /* x_dev = M(y_dev) = G^H(y_dev): chirp-scaling focusing (Section III-A Eq. (10),
  * Section III-D): azimuth FFT, x H1, range FFT, x H2, range IFFT, x H3, azimuth
- * IFFT.  Same layout and aliasing rules as csar_G. */
+ * IFFT (on a CSAR_PLAN_RDA plan: azimuth FFT, range compression, RCMC C, x P_eta,
+ * azimuth IFFT).  Same layout and aliasing rules as csar_G. */
 csar_status csar_M(csar_plan plan, const void* y_dev, void* x_dev, void* stream);
 
 /* One iteration of Algorithm 1 (Eq. (25)) on device data:
