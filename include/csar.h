@@ -217,8 +217,8 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
                              float* theta_bar_dev, void* X0bar_dev, void* stream);
 
 /* y_dev = G(x_dev) without any device allocation, for callers that cannot call
- * cudaMalloc (their allocator is owned by a host framework, they run inside stream
- * capture, or they must not allocate after start-up).  The paper has no counterpart:
+ * cudaMalloc (their device memory is owned and handed out by a host framework, or
+ * they must not allocate after start-up).  The paper has no counterpart:
  * it is a deployment variant of csar_G.  Same operator, layout and aliasing rules as
  * csar_G, but no plan: the phase coefficients and FFT twiddles that a plan would keep
  * in allocated memory go into one static device array of the library (about 580 KiB

@@ -4,8 +4,8 @@
 // csar_G needs per-row phase coefficients and FFT twiddles in device memory; a plan
 // allocates them.  Some callers cannot call cudaMalloc at all: code running where
 // the allocator is owned by someone else (a host framework that hands out only its
-// own buffers), code inside stream capture, or embedded/real-time callers that must
-// not allocate after start-up.  csar_G_noalloc keeps those tables in one file-scope
+// own buffers), or embedded/real-time callers that must not allocate after start-up.
+// csar_G_noalloc keeps those tables in one file-scope
 // static device array instead, so it allocates nothing: the caller passes only its
 // input and output buffers.
 #include <cuda_runtime.h>

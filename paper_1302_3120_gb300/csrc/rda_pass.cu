@@ -221,12 +221,15 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
       // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
       __syncthreads();   // the mbarrier is initialised
       const uint32_t mb = smem_addr(mbar);
-      if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
+      bool landed = mbar_wait_for(mb, 0u, 1000000000ull);
+      if (!landed) {
         // the copy did not land within a second: report it, and give it one more second
-        // before the buffer is reused
         atomicOr(&a.ctl->err, kErrTimeout);
-        mbar_wait_for(mb, 0u, 1000000000ull);
+        landed = mbar_wait_for(mb, 0u, 1000000000ull);
       }
+      // if any thread still saw no completion, the whole CTA leaves without touching the
+      // buffer again (the latched error marks the result invalid)
+      if (__syncthreads_or(!landed)) return;
       const float2* ys = sm + w * N;
       float sq = 0.f;
       bool bad = false;

@@ -84,12 +84,15 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
     bool bad = false;
     if constexpr (kBulkY<N>) {
       const uint32_t mb = smem_addr(mbar);   // initialised before the Gamma-table barrier
-      if (!mbar_wait_for(mb, 0u, 1000000000ull)) {
+      bool landed = mbar_wait_for(mb, 0u, 1000000000ull);
+      if (!landed) {
         // the copy did not land within a second: report it, and give it one more second
-        // before the buffer is reused
         atomicOr(&a.ctl->err, kErrTimeout);
-        mbar_wait_for(mb, 0u, 1000000000ull);
+        landed = mbar_wait_for(mb, 0u, 1000000000ull);
       }
+      // if any thread still saw no completion, the whole CTA leaves without touching the
+      // buffer again (the latched error marks the result invalid)
+      if (__syncthreads_or(!landed)) return;
       const float2* ys = sm + w * N;
 #pragma unroll
       for (int s = 0; s < R; ++s) {
