@@ -83,6 +83,48 @@ def test_kth_largest_against_counting(k):
         assert np.count_nonzero(ita.soft_threshold(b, s)) <= k
 
 
+@pytest.mark.parametrize("k", [0, 1, 5, 37, 64, 100])
+def test_top_k_support_against_sorting_and_counting(k):
+    """top_k_support picks exactly min(k, n) entries: those first in the order of
+    decreasing magnitude with ties broken by the lower flat index (brute force over
+    the sorted index list), and each picked entry has fewer than k strictly larger
+    magnitudes (counting).  Exact ties are planted (|conj z| = |-z| = |z| exactly)."""
+    rng = np.random.default_rng(13)
+    v = _rand(rng, (8, 8))
+    v.flat[10] = np.conj(v.flat[20])
+    v.flat[30] = -v.flat[20]
+    v.flat[40] = v.flat[41]
+    sel = ita.top_k_support(v, k)
+    assert sel.shape == v.shape and sel.dtype == bool
+    assert int(sel.sum()) == min(k, v.size)
+    mag = np.abs(v).reshape(-1)
+    order = sorted(range(v.size), key=lambda i: (-mag[i], i))
+    assert set(np.flatnonzero(sel).tolist()) == set(order[:k])
+    for i in np.flatnonzero(sel):
+        assert np.sum(mag > mag[i]) < k
+    if 0 < k < v.size:
+        assert mag[sel.reshape(-1)].min() >= mag[~sel.reshape(-1)].max()
+
+
+def test_add_noise_sets_requested_snr():
+    """add_noise: the SNR measured on its output (mean |s|^2 over the full grid over the
+    mean power of what it added) is within 0.1 dB of the request, on a 256^2 point-target
+    echo whose mean power is far from 1 (so an amplitude-for-power slip shows), at
+    10, 20 and 30 dB; the noise covers every element of the grid."""
+    g = synth.airborne(256, 256)
+    rng = np.random.default_rng(12)
+    rows, cols, amps = synth.point_targets(rng, 256, 256, 5)
+    s = echo.point_echo(g, rows, cols, 3.0 * amps)
+    p = float(np.mean(np.abs(s) ** 2))
+    assert abs(np.log10(p)) > 0.3
+    for snr in (10.0, 20.0, 30.0):
+        out = echo.add_noise(synth.cn_noise(rng, s.shape), s, snr)
+        n = out - s
+        meas = 10.0 * np.log10(p / float(np.mean(np.abs(n) ** 2)))
+        assert abs(meas - snr) < 0.1, (snr, meas)
+        assert np.count_nonzero(n) == n.size
+
+
 # ----------------------------------------------------------------------------- ITA
 
 @pytest.mark.parametrize("kind", ["soft", "half", "hard"])

@@ -8,7 +8,7 @@ import pytest
 import synth
 import test_oracle_ita as ita_pins
 import test_oracle_operators as op_pins
-from oracle import csa, ita
+from oracle import csa, echo, ita
 
 C = 299792458.0
 
@@ -110,10 +110,12 @@ ITA_PINS = [
     lambda: ita_pins.test_full_sampling_closed_form("soft"),
     ita_pins.test_first_iterate_is_threshold_of_masked_mf,
     ita_pins.test_niht_step_properties,
+    lambda: ita_pins.test_top_k_support_against_sorting_and_counting(5),
 ]
 
 _soft, _half, _kth, _niht = ita.soft_threshold, ita.half_threshold, ita.kth_largest_magnitude, ita.niht_step
 _hard = ita.hard_threshold
+_top_k = ita.top_k_support
 
 
 def _ita_iteration_unmasked(g, y, mask, x, k, mu_mode="fixed", mu=1.0, kind="soft", ops="csa"):
@@ -132,6 +134,9 @@ ITA_MUTATIONS = {
     "K-th instead of (K+1)-th": ("kth_largest_magnitude", lambda b, k: _kth(b, max(k - 1, 0))),
     "NIHT ratio inverted": ("niht_step", lambda g, m, dx, sup, ops="csa": 1.0 / _niht(g, m, dx, sup, ops)),
     "mask dropped from residue": ("ita_iteration", _ita_iteration_unmasked),
+    "top-K support picks the smallest": (
+        "top_k_support", lambda v, k: _top_k(-1.0 / (np.abs(v) + 1e-300), k)),
+    "top-K support keeps one too many": ("top_k_support", lambda v, k: _top_k(v, k + 1)),
 }
 
 
@@ -140,3 +145,33 @@ def test_ita_mutation_is_caught(name, monkeypatch):
     attr, fn = ITA_MUTATIONS[name]
     monkeypatch.setattr(ita, attr, fn)
     assert _some_pin_fails(ITA_PINS), name
+
+
+ECHO_PINS = [ita_pins.test_add_noise_sets_requested_snr]
+_add_noise = echo.add_noise
+
+
+def _noise_power_as_amplitude(rng_noise, s, snr_db):
+    p = float(np.mean(np.abs(s) ** 2))
+    return s + (p / 10.0 ** (snr_db / 10.0)) * rng_noise
+
+
+def _noise_db_as_amplitude_ratio(rng_noise, s, snr_db):
+    p = float(np.mean(np.abs(s) ** 2))
+    return s + np.sqrt(p) / 10.0 ** (snr_db / 10.0) * rng_noise
+
+
+ECHO_MUTATIONS = {
+    "noise sigma from the power, not its square root": ("add_noise", _noise_power_as_amplitude),
+    "noise SNR in dB taken as an amplitude ratio": ("add_noise", _noise_db_as_amplitude_ratio),
+    "noise power from the peak, not the mean": (
+        "add_noise", lambda n, s, snr: _add_noise(n * np.sqrt(np.max(np.abs(s) ** 2) /
+                                                              np.mean(np.abs(s) ** 2)), s, snr)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ECHO_MUTATIONS))
+def test_echo_mutation_is_caught(name, monkeypatch):
+    attr, fn = ECHO_MUTATIONS[name]
+    monkeypatch.setattr(echo, attr, fn)
+    assert _some_pin_fails(ECHO_PINS), name
