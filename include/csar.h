@@ -287,6 +287,24 @@ csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* cho
  * has no counterpart: it checks that no device-side wait of the library can hang. */
 csar_status csar_selftest_wait_timeout(int32_t limit_ms);
 
+/* ---- Test hook of the threshold rule ---------------------------------------------
+ * Section IV-B sets sigma = |b|_(K+1); the selection finds it as the (K+1)-th largest
+ * of the fp32 keys key(b) = bits(|b|^2) over the union of the support and the
+ * candidates.  With the record enabled (capacity > 0 entries; 0 disables and frees it),
+ * every ITA iteration on the plan (csar_ita_step, csar_solve, csar_solve_profile)
+ * overwrites a device record of that union right after the threshold: each element's
+ * flat index, b (float re, im) and key exactly as the selection kernels formed them,
+ * the union size and the iteration's sigma^2 key, mu and sigma.  Enabling synchronises
+ * the device, drops the plan's captured graphs and allocates 16 bytes per entry.
+ * csar_debug_selection_read synchronises and copies min(union size, capacity of the
+ * record, `capacity`) entries into the host arrays (any may be NULL; b_host holds
+ * 2 floats per entry); *count receives the union size.  CSAR_E_INTERNAL if the union
+ * was larger than the record. */
+csar_status csar_debug_selection_enable(csar_plan plan, int64_t capacity);
+csar_status csar_debug_selection_read(csar_plan plan, uint32_t* idx_host, float* b_host,
+                                      uint32_t* key_host, int64_t capacity, int64_t* count,
+                                      uint32_t* sigma2_key, float* mu, float* sigma);
+
 /* Synchronise the plan's device and report (and clear) any latched device-side
  * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, CSAR_E_TIMEOUT, ...). */
 csar_status csar_plan_check(csar_plan plan);

@@ -55,7 +55,8 @@ EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_it
            "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
            "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
-           "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout", "csar_echo_points")
+           "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout", "csar_echo_points",
+           "csar_debug_selection_enable", "csar_debug_selection_read")
 
 
 def _load() -> ctypes.CDLL:
@@ -86,13 +87,19 @@ def _load() -> ctypes.CDLL:
     lib.csar_autotune.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(i32)]
     lib.csar_selftest_wait_timeout.argtypes = [i32]
     lib.csar_echo_points.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int64, vp, i32, vp]
+    lib.csar_debug_selection_enable.argtypes = [vp, ctypes.c_int64]
+    lib.csar_debug_selection_read.argtypes = [vp, vp, vp, vp, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(u32),
+                                              ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(ctypes.c_float)]
     lib.csar_last_error.restype = ctypes.c_char_p
     lib.csar_version.restype = i32
     for name in ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_ita_step",
                  "csar_solve", "csar_solve_host", "csar_solve_profile", "csar_plan_check",
                  "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc",
                  "csar_batch_create", "csar_batch_destroy", "csar_solve_batched", "csar_batch_check",
-                 "csar_autotune", "csar_echo_points"):
+                 "csar_autotune", "csar_echo_points", "csar_debug_selection_enable",
+                 "csar_debug_selection_read"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -298,6 +305,29 @@ def csar_solve_profile(plan: Plan, Y, mask_bits, K: int, iters: int, mu_mode="fi
 
 def csar_plan_check(plan: Plan) -> None:
     _check(lib.csar_plan_check(plan.handle), "csar_plan_check")
+
+
+def csar_debug_selection_enable(plan: Plan, capacity: int) -> None:
+    """Record the union the selection ranks in every later ITA iteration of the plan
+    (capacity entries; 0 turns the record off)."""
+    _check(lib.csar_debug_selection_enable(plan.handle, int(capacity)), "csar_debug_selection_enable")
+
+
+def csar_debug_selection_read(plan: Plan, capacity: int) -> dict:
+    """The last recorded union: flat indices, b (complex64) and keys (uint32) as the
+    selection kernels formed them, plus sigma2_key, mu and sigma of that iteration."""
+    idx = np.zeros(capacity, dtype=np.uint32)
+    b = np.zeros(capacity, dtype=np.complex64)
+    key = np.zeros(capacity, dtype=np.uint32)
+    cnt, s2 = ctypes.c_int64(0), ctypes.c_uint32(0)
+    mu, sig = ctypes.c_float(0), ctypes.c_float(0)
+    _check(lib.csar_debug_selection_read(plan.handle, idx.ctypes.data, b.ctypes.data, key.ctypes.data,
+                                         int(capacity), ctypes.byref(cnt), ctypes.byref(s2),
+                                         ctypes.byref(mu), ctypes.byref(sig)),
+           "csar_debug_selection_read")
+    m = min(int(cnt.value), capacity)
+    return {"idx": idx[:m], "b": b[:m], "key": key[:m], "count": int(cnt.value),
+            "sigma2_key": int(s2.value), "mu": float(mu.value), "sigma": float(sig.value)}
 
 
 def csar_version() -> int:

@@ -134,9 +134,10 @@ struct GraphKey {
   uint32_t cand_cap = 0;
   IterStat* stats = nullptr;
   const void* ck = nullptr;
+  const void* dump = nullptr;
   bool operator==(const GraphKey& o) const {
     return y == o.y && mask == o.mask && K == o.K && mu_mode == o.mu_mode && thresh == o.thresh &&
-           mu == o.mu && cand_cap == o.cand_cap && stats == o.stats && ck == o.ck;
+           mu == o.mu && cand_cap == o.cand_cap && stats == o.stats && ck == o.ck && dump == o.dump;
   }
 };
 
@@ -327,6 +328,7 @@ struct csar_plan_s {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   GraphKey key[2];
   bool use_graphs = true;
+  SelDump dump;                   // selection record (csar_debug_selection_*), off when idx is null
 };
 
 // A batch of independent patches: one plan per patch; each ITA iteration of the whole
@@ -644,6 +646,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   } else {
     LK(multi(s));
   }
+  if (plan->dump.idx) LK(launch_sel_dump(sa, plan->dump, s));
   if (o.mu_mode == CSAR_MU_NIHT) {
     // first iteration: Gamma = the top-K list just written (raw Delta X values)
     ColArgs g = col_args(plan);
@@ -784,6 +787,7 @@ csar_status run_iterations(csar_plan plan, const float2* y, const uint32_t* mask
       k.cand_cap = plan->b.cand_cap;
       k.stats = plan->b.stats;
       k.ck = plan->b.ck_active ? (const void*)plan->b.ck_idx : nullptr;
+      k.dump = plan->dump.idx;
       if (!plan->exec[cur] || !(plan->key[cur] == k)) {
         if (plan->exec[cur]) cudaGraphExecDestroy(plan->exec[cur]);
         plan->exec[cur] = nullptr;
@@ -1008,6 +1012,9 @@ csar_status csar_plan_destroy(csar_plan plan) {
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
   if (plan->cond_stream) cudaStreamDestroy(plan->cond_stream);
   free_buffers(plan->b);
+  void* dump[] = {plan->dump.idx, plan->dump.b, plan->dump.key, plan->dump.count, plan->dump.ctl};
+  for (void* q : dump)
+    if (q) cudaFree(q);
   if (plan->coef_g) cudaFree(plan->coef_g);
   if (plan->coef_m) cudaFree(plan->coef_m);
   if (plan->rda_rg_g) cudaFree(plan->rda_rg_g);
@@ -1084,6 +1091,60 @@ csar_status csar_plan_check(csar_plan plan) {
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   DeviceGuard dg(plan->dev);
   CK(cudaDeviceSynchronize());
+  return latched(plan);
+}
+
+csar_status csar_debug_selection_enable(csar_plan plan, int64_t capacity) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (capacity < 0 || capacity > plan->n + (int64_t)plan->b.cand_cap + (int64_t(1) << 24))
+    return fail(CSAR_E_INVALID, "capacity out of range");
+  DeviceGuard dg(plan->dev);
+  CK(cudaDeviceSynchronize());
+  drop_graphs(plan);
+  SelDump& d = plan->dump;
+  void* old[] = {d.idx, d.b, d.key, d.count, d.ctl};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  d = SelDump();
+  if (capacity == 0) return CSAR_OK;
+  SelDump n;
+  cudaError_t e = dalloc(&n.idx, (size_t)capacity);
+  if (e == cudaSuccess) e = dalloc(&n.b, (size_t)capacity);
+  if (e == cudaSuccess) e = dalloc(&n.key, (size_t)capacity);
+  if (e == cudaSuccess) e = dalloc(&n.count, 1);
+  if (e == cudaSuccess) e = dalloc(&n.ctl, 1);
+  if (e != cudaSuccess) {
+    void* part[] = {n.idx, n.b, n.key, n.count, n.ctl};
+    for (void* q : part)
+      if (q) cudaFree(q);
+    return fail(CSAR_E_OOM, "selection record: %s", cudaGetErrorString(e));
+  }
+  n.cap = (uint32_t)capacity;
+  d = n;
+  return CSAR_OK;
+}
+
+csar_status csar_debug_selection_read(csar_plan plan, uint32_t* idx_host, float* b_host, uint32_t* key_host,
+                                      int64_t capacity, int64_t* count, uint32_t* sigma2_key, float* mu,
+                                      float* sigma) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!plan->dump.idx) return fail(CSAR_E_INVALID, "selection record not enabled");
+  if (!count || !sigma2_key || !mu || !sigma) return fail(CSAR_E_INVALID, "null output pointer");
+  DeviceGuard dg(plan->dev);
+  CK(cudaDeviceSynchronize());
+  uint32_t nu = 0;
+  Ctl c;
+  CK(cudaMemcpy(&nu, plan->dump.count, sizeof nu, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&c, plan->dump.ctl, sizeof c, cudaMemcpyDeviceToHost));
+  *count = nu;
+  *sigma2_key = c.sigma2_key;
+  *mu = c.mu;
+  *sigma = c.sigma;
+  const int64_t m = std::min<int64_t>({(int64_t)nu, (int64_t)plan->dump.cap, capacity});
+  if (m > 0 && idx_host) CK(cudaMemcpy(idx_host, plan->dump.idx, m * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (m > 0 && b_host) CK(cudaMemcpy(b_host, plan->dump.b, m * sizeof(float2), cudaMemcpyDeviceToHost));
+  if (m > 0 && key_host) CK(cudaMemcpy(key_host, plan->dump.key, m * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if ((int64_t)nu > (int64_t)plan->dump.cap) return fail(CSAR_E_INTERNAL, "union larger than the record's capacity");
   return latched(plan);
 }
 

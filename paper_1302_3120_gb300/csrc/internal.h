@@ -251,6 +251,19 @@ struct SelArgs {
   int fused_ok;               // 0: always the grid-wide path (CSAR_SEL_FUSED=0)
 };
 
+// Record of the union the selection ranked (tests of the exact lambda rule): each
+// element's flat index, b and key, as the selection kernels formed them, the union size
+// and the control block right after the threshold.
+struct SelDump {
+  uint32_t* idx = nullptr;
+  float2* b = nullptr;
+  uint32_t* key = nullptr;
+  uint32_t* count = nullptr;
+  Ctl* ctl = nullptr;
+  uint32_t cap = 0;
+};
+cudaError_t launch_sel_dump(const SelArgs& a, const SelDump& d, cudaStream_t s);
+
 cudaError_t launch_sel_check(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_sel_check2(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_sel_round(const SelArgs& a, int level, cudaStream_t s);

@@ -111,6 +111,32 @@ __device__ int find_bin(const uint32_t* h, int nb, uint64_t target, uint64_t* ab
   return res_b;
 }
 
+// ------------------------------------------------------------------ selection record
+// Every union element's index, b and key exactly as the ranking kernels form them
+// (union_b, key_of), plus the union size and the control block (sigma2_key, mu, sigma).
+__global__ void __launch_bounds__(kGridThreads) k_sel_dump(SelArgs a, SelDump d) {
+  const Ctl* c = a.ctl;
+  const uint32_t nu = union_size(c, a.cand_cap), nx = c->nx;
+  const float mu = c->mu;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *d.count = nu;
+    *d.ctl = *c;
+  }
+  const uint32_t lim = nu < d.cap ? nu : d.cap;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < lim; e += gridDim.x * blockDim.x) {
+    uint32_t i;
+    const float2 b = union_b(a, e, nx, mu, &i);
+    d.idx[e] = i;
+    d.b[e] = b;
+    d.key[e] = key_of(b);
+  }
+}
+
+cudaError_t launch_sel_dump(const SelArgs& a, const SelDump& d, cudaStream_t s) {
+  k_sel_dump<<<256, kGridThreads, 0, s>>>(a, d);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ check / repass
 // Capacity check of a re-pass with cut bin lb: off-support keys at or above it.
 __device__ void check_capacity(const SelArgs& a, int lb) {

@@ -1,6 +1,8 @@
 """GPU parity of the ITA (Algorithm 1 / Eq. (25)) against the FP64 oracle: single
 iterations with every step/threshold mode, full solves on the 256^2 point-target
 workload and on distributed scenes, the degenerate cases, and the 8192^2 workload."""
+import os
+
 import numpy as np
 import pytest
 
@@ -9,6 +11,8 @@ from gpu_helpers import crand, dev, dev_mask, host, lib
 from oracle import csa, echo, ita, metrics
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def assert_iterate_matches(x_gpu, x_ref, b_ref, sigma_ref, rel=1e-4, band=1e-4):
@@ -24,6 +28,28 @@ def assert_iterate_matches(x_gpu, x_ref, b_ref, sigma_ref, rel=1e-4, band=1e-4):
         assert metrics.rel_l2(x_gpu, x_ref) < rel
     else:
         assert np.abs(x_gpu).max() < 1e-6
+
+
+def oracle_solve(g, y, mask, K, iters, **kw):
+    """The oracle's Algorithm 1 for `iters` iterations, also returning b and sigma of the
+    last iteration (for the support rule of the final image)."""
+    x, st = ita.ita(g, y, mask, K, iters - 1, **kw)
+    x, last, b = ita.ita_iteration(g, y, np.asarray(mask, dtype=np.float64), x, K, return_b=True,
+                                   **{k: v for k, v in kw.items() if k != "x0"})
+    return x, st + [last], b, last.sigma
+
+
+def assert_final_matches_golden(xg, gold, rel=1e-3):
+    """Final image against a stored oracle result: identical support outside the stored
+    band (| |b| - sigma | <= 1e-4 sigma at the last iteration), values within rel."""
+    flat = xg.reshape(-1)
+    ref = np.zeros(flat.size, np.complex128)
+    ref[gold["idx"]] = gold["val"]
+    band = np.zeros(flat.size, dtype=bool)
+    band[gold["band"]] = True
+    diff = (flat != 0) != (ref != 0)
+    assert not np.any(diff & ~band), int(np.sum(diff & ~band))
+    assert metrics.rel_l2(flat, ref) < rel
 
 
 def _problem(seed, na=256, nr=256, frac=0.01, rate=0.5, geom=synth.airborne, noise_db=None):
@@ -77,12 +103,12 @@ def test_config1_point_targets_solve():
     s = echo.add_noise(synth.cn_noise(rng, s.shape), s, 30.0)
     mask = synth.bernoulli_mask(rng, 256, 256, 0.5)
     y = mask * s
-    x_ref, st_ref = ita.ita(g, y, mask, 5, 100)
+    x_ref, st_ref, b_ref, s_ref = oracle_solve(g, y, mask, 5, 100)
     plan = csar.csar_plan_create(g)
     X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), 5, 100, stats=True)
     xg = host(X)
     assert set(zip(*np.nonzero(xg))) == set(zip(rows.tolist(), cols.tolist()))
-    assert metrics.rel_l2(xg, x_ref) < 1e-3
+    assert_iterate_matches(xg, x_ref, b_ref, s_ref, rel=1e-3)
     sig_ref = np.array([s_.sigma for s_ in st_ref])
     assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-3
     res_ref = np.array([s_.resid_sq for s_ in st_ref])
@@ -98,12 +124,12 @@ def test_distributed_scene_solve(mu_mode, kind):
     g, xt, y, mask = _problem(21, 512, 512, noise_db=20.0)
     K = int(round(0.01 * 512 * 512))
     iters = 30
-    x_ref, st_ref = ita.ita(g, y, mask, K, iters, mu_mode=mu_mode, kind=kind)
+    x_ref, st_ref, b_ref, s_ref = oracle_solve(g, y, mask, K, iters, mu_mode=mu_mode, kind=kind)
     plan = csar.csar_plan_create(g)
     X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, iters, mu_mode=mu_mode, thresh=kind,
                             stats=True)
     xg = host(X)
-    assert metrics.rel_l2(xg, x_ref) < 1e-3
+    assert_iterate_matches(xg, x_ref, b_ref, s_ref, rel=1e-3)
     assert np.all(st["nnz"] <= K)
     if mu_mode == "niht":
         # with hard thresholding the support-restricted gradient Delta X_Gamma vanishes
@@ -164,9 +190,11 @@ def test_host_buffer_entry_point():
 
 def test_full_size_spaceborne_iterations():
     """8192^2 spaceborne workload (2000 3x3 targets over -25 dB clutter, 40% sampling,
-    K = 20000) in the launch configuration the benchmark times: 2 iterations against
-    the oracle."""
+    K = 20000) in the launch configuration the benchmark times: 20 iterations against
+    the stored FP64 oracle result (tests/golden/make_ita_goldens.py), final image with
+    the support rule, sigma_i and ||r_i||^2 at every iteration."""
     csar = lib()
+    gold = np.load(os.path.join(GOLDEN, "config3_it20.npz"))
     g = synth.spaceborne(8192, 8192)
     rng = np.random.default_rng(0)
     x = synth.targets_over_clutter(rng, 8192, 8192)
@@ -174,15 +202,14 @@ def test_full_size_spaceborne_iterations():
     y = csa.observe_G(g, x)
     del x
     y *= mask
-    K = 20000
-    x_ref = np.zeros((8192, 8192), complex)
-    for _ in range(2):
-        x_ref, st, b_ref = ita.ita_iteration(g, y, mask, x_ref, K, return_b=True)
+    K, iters = int(gold["K"]), int(gold["iters"])
     plan = csar.csar_plan_create(g)
-    X, stg = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 2, stats=True)
+    X, stg = csar.csar_solve(plan, dev(y), dev_mask(mask), K, iters, stats=True)
+    del y
     xg = host(X)
-    assert abs(stg["sigma"][-1] - st.sigma) <= 1e-4 * st.sigma
-    assert_iterate_matches(xg, x_ref, b_ref, st.sigma, rel=1e-3)
+    assert np.max(np.abs(stg["sigma"] - gold["sigma"]) / gold["sigma"]) <= 1e-4
+    assert np.max(np.abs(stg["resid_sq"] - gold["resid_sq"]) / gold["resid_sq"]) <= 1e-4
+    assert_final_matches_golden(xg, gold)
 
 
 def test_dense_iterate_groups_are_deterministic():
@@ -196,8 +223,8 @@ def test_dense_iterate_groups_are_deterministic():
     a = host(csar.csar_solve(plan, Y, M, K, 8))
     b = host(csar.csar_solve(plan, Y, M, K, 8))
     assert np.array_equal(a, b)
-    x_ref, _ = ita.ita(g, y, mask, K, 8)
-    assert metrics.rel_l2(a, x_ref) < 1e-3
+    x_ref, _, b_ref, s_ref = oracle_solve(g, y, mask, K, 8)
+    assert_iterate_matches(a, x_ref, b_ref, s_ref, rel=1e-3)
 
 
 @pytest.mark.parametrize("na,nr,p,half", [
@@ -214,12 +241,12 @@ def test_every_column_configuration(na, nr, p, half):
     csar = lib()
     g, xt, y, mask = _problem(31, na, nr, frac=0.02)
     K = int(round(0.02 * na * nr))
-    x_ref, st_ref = ita.ita(g, y, mask, K, 3, mu_mode="niht")
+    x_ref, st_ref, b_ref, s_ref = oracle_solve(g, y, mask, K, 3, mu_mode="niht")
     flags = csar.plan_col_cluster(p) | {0: 0, 1: csar.PLAN_COL_HALF_TILE, 2: csar.PLAN_COL_WIDE_TILE}[half]
     plan = csar.csar_plan_create(g, flags=flags)
     X, st = csar.csar_solve(plan, dev(y), dev_mask(mask), K, 3, mu_mode="niht", stats=True)
     csar.csar_plan_check(plan)
-    assert metrics.rel_l2(host(X), x_ref) < 1e-3
+    assert_iterate_matches(host(X), x_ref, b_ref, s_ref, rel=1e-3)
     sig_ref = np.array([s_.sigma for s_ in st_ref])
     assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-4
 
@@ -240,7 +267,7 @@ def test_sharp_threshold_drops(rate, iters):
     x.flat[idx] = 10 * np.exp(2j * np.pi * rng.random(k))
     mask = synth.bernoulli_mask(rng, na, nr, rate)
     y = mask * csa.observe_G(g, x)
-    x_ref, st_ref = ita.ita(g, y, mask, k, iters)
+    x_ref, st_ref, b_ref, s_ref = oracle_solve(g, y, mask, k, iters)
     sig_ref = np.array([s_.sigma for s_ in st_ref])
     assert np.max(sig_ref[:-1] / sig_ref[1:]) > (6.0 if rate > 0.9 else 3.0)
     plan = csar.csar_plan_create(g)
@@ -249,7 +276,7 @@ def test_sharp_threshold_drops(rate, iters):
     assert np.max(np.abs(st["sigma"] - sig_ref) / sig_ref) < 1e-2
     xg = host(X)
     assert set(np.flatnonzero(xg)) == set(np.flatnonzero(x_ref))
-    assert metrics.rel_l2(xg, x_ref) < 1e-3
+    assert_iterate_matches(xg, x_ref, b_ref, s_ref, rel=1e-3)
 
 
 @pytest.mark.parametrize("rate", [0.3, 0.5])
@@ -257,7 +284,9 @@ def test_config2_precision_study(rate):
     """2048^2 airborne precision study: 1% Rayleigh scene (sigma = 1), echo G(X) + 20 dB
     noise, Bernoulli sampling at 30% and 50%, K = 41943.  Per-operator rel-L2 of the
     complex64 G and M against the FP64 oracle (<= 1e-5) and the ITA against the oracle
-    over 10 iterations (final image <= 1e-3, sigma_i <= 1e-4); the values are printed."""
+    over the configuration's 200 iterations (stored oracle result,
+    tests/golden/make_ita_goldens.py): final image <= 1e-3 with the support rule,
+    sigma_i and ||r_i||^2 <= 1e-4 at every iteration; the values are printed."""
     csar = lib()
     na = nr = 2048
     g = synth.airborne(na, nr)
@@ -270,15 +299,19 @@ def test_config2_precision_study(rate):
     plan = csar.csar_plan_create(g)
     e_g = metrics.rel_l2(host(csar.csar_G(plan, dev(x))), y_clean)
     e_m = metrics.rel_l2(host(csar.csar_M(plan, dev(ys))), csa.focus_M(g, ys))
-    K, iters = 41943, 10
-    x_ref, st_ref = ita.ita(g, ys, mask, K, iters)
+    gold = np.load(os.path.join(GOLDEN, f"config2_r{int(round(rate * 100))}.npz"))
+    K, iters = int(gold["K"]), int(gold["iters"])
     X, st = csar.csar_solve(plan, dev(ys), dev_mask(mask), K, iters, stats=True)
     csar.csar_plan_check(plan)
-    e_x = metrics.rel_l2(host(X), x_ref)
-    sig_ref = np.array([s_.sigma for s_ in st_ref])
-    e_s = float(np.max(np.abs(st["sigma"] - sig_ref) / sig_ref))
+    xg = host(X)
+    ref = np.zeros(na * nr, complex)
+    ref[gold["idx"]] = gold["val"]
+    e_x = metrics.rel_l2(xg.reshape(-1), ref)
+    e_s = float(np.max(np.abs(st["sigma"] - gold["sigma"]) / gold["sigma"]))
+    e_r = float(np.max(np.abs(st["resid_sq"] - gold["resid_sq"]) / gold["resid_sq"]))
     print(f"\nconfig 2, {int(rate * 100)}% sampling: rel-L2 G {e_g:.2e}, M {e_m:.2e}, "
-          f"X^({iters}) {e_x:.2e}; max sigma rel err {e_s:.2e}")
+          f"X^({iters}) {e_x:.2e}; max sigma rel err {e_s:.2e}, max resid rel err {e_r:.2e}")
     assert e_g < 1e-5 and e_m < 1e-5
-    assert e_x < 1e-3 and e_s < 1e-4
-    assert np.count_nonzero(host(X)) <= K
+    assert e_s < 1e-4 and e_r < 1e-4
+    assert_final_matches_golden(xg, gold)
+    assert np.count_nonzero(xg) <= K
