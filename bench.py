@@ -152,20 +152,76 @@ def make_inputs(csar, plan, seed: int):
     return x, y, md, bits
 
 
-def cpu_baseline_oracle(x_scene: np.ndarray, bits: np.ndarray, iters: int = 1):
-    """The FP64 oracle on the host cores: `iters` ITA iterations of the same workload.
-    Returns (seconds per iteration, cores)."""
+def cpu_baseline_oracle(x_scene: np.ndarray, bits: np.ndarray, iters: int = 1, workers_list=(0,)):
+    """The FP64 oracle on the host cores: `iters` ITA iterations of the same workload for
+    each FFT worker count in workers_list (0: every core).  Returns [(seconds per
+    iteration, workers)]."""
     from oracle import csa, ita
     g = synth.spaceborne(N_AZ, N_RG)
     mask = np.unpackbits(bits.view(np.uint8), bitorder="little").astype(bool).reshape(N_AZ, N_RG)
     y = csa.observe_G(g, x_scene.astype(np.complex128))
     y *= mask
-    x = np.zeros((N_AZ, N_RG), np.complex128)
-    t0 = time.perf_counter()
-    for _ in range(iters):
-        x, _ = ita.ita_iteration(g, y, mask, x, K_SPARSITY)
-    dt = (time.perf_counter() - t0) / iters
-    return dt, os.cpu_count() or 1
+    out = []
+    saved = csa._WORKERS
+    try:
+        for w in workers_list:
+            csa._WORKERS = w or (os.cpu_count() or 1)
+            x = np.zeros((N_AZ, N_RG), np.complex128)
+            t0 = time.perf_counter()
+            for _ in range(iters):
+                x, _ = ita.ita_iteration(g, y, mask, x, K_SPARSITY)
+            out.append(((time.perf_counter() - t0) / iters, csa._WORKERS))
+    finally:
+        csa._WORKERS = saved
+    return out
+
+
+def cufft_comparison(csar, plan, y, md, steps: int):
+    """The cuFFT-based comparison build (paper_1302_3120_gb300/compare/cufft_ita.cu: the
+    same iteration in dense form with cuFFT C2C transforms, elementwise phase kernels and a
+    three-round radix select), timed on the same GPU and inputs, plus its agreement with
+    the library after 20 iterations.  Never part of the library's path."""
+    import ctypes
+    import torch
+    path = os.path.join(ROOT, "paper_1302_3120_gb300", "libcsar_cufft.so")
+    if not os.path.exists(path):
+        return {"unavailable": "libcsar_cufft.so was not built"}
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.csar_cufft_create.argtypes = [ctypes.POINTER(csar.Params), ctypes.POINTER(vp)]
+    lib.csar_cufft_solve.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, vp]
+    lib.csar_cufft_destroy.argtypes = [vp]
+    lib.csar_cufft_last_error.restype = ctypes.c_char_p
+    p = csar.params_of(synth.spaceborne(N_AZ, N_RG))
+    h = vp()
+    if lib.csar_cufft_create(ctypes.byref(p), ctypes.byref(h)) != 0:
+        return {"unavailable": lib.csar_cufft_last_error().decode()}
+    stream = torch.cuda.current_stream()
+    sp = vp(stream.cuda_stream)
+    xc = torch.empty_like(y)
+
+    def solve(iters):
+        st = lib.csar_cufft_solve(h, vp(y.data_ptr()), vp(md.data_ptr()), vp(xc.data_ptr()),
+                                  K_SPARSITY, iters, 1.0, sp)
+        if st != 0:
+            raise RuntimeError(lib.csar_cufft_last_error().decode())
+    try:
+        solve(3)
+        ms = _event_ms(lambda: solve(steps), stream)
+        solve(20)
+        torch.cuda.synchronize()
+        x_cmp = xc.cpu().numpy()
+        x_lib = csar.csar_solve(plan, y, md, K_SPARSITY, 20).cpu().numpy()
+    finally:
+        lib.csar_cufft_destroy(h)
+    d = np.linalg.norm(x_cmp - x_lib) / max(np.linalg.norm(x_lib), 1e-30)
+    same = int(np.count_nonzero((x_cmp != 0) == (x_lib != 0)))
+    return {"value": steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "rel_l2_vs_library_20_iters": float(d),
+            "support_agreement_20_iters": same / x_lib.size,
+            "what": "same inputs and GPU; dense ITA with cuFFT C2C (8 transforms), 6 phase, "
+                    "residue, step+histogram, 2 histogram, 3 pick, threshold kernels per "
+                    "iteration, captured in one CUDA graph"}
 
 
 def run_reference(args, world, rank):
@@ -376,6 +432,7 @@ def main():
                     help="operator pair of --workload operators and of the ITA workload "
                          "(rda: CS-RDA; no CPU baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison build")
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--size", type=int, default=8192,
                     help="profiling only: azimuth size of a smaller case of the same workload")
@@ -491,15 +548,22 @@ def main():
            "note": f"{calls} csar_solve_host calls of {per_call} iterations each (echo and "
                    "mask copied in, image copied out once per call)"}
 
-    cpu = None
+    cmp = None
+    if rank == 0 and world == 1 and not rda and not args.no_cufft:
+        cmp = cufft_comparison(csar, plan, y, md, min(args.steps, 200))
+
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not rda:
         del y, X
         torch.cuda.empty_cache()
-        dt, cores = cpu_baseline_oracle(x_scene, bits, args.cpu_iters)
+        res = cpu_baseline_oracle(x_scene, bits, args.cpu_iters, (0, 1))
+        (dt, cores), (dt1, _) = res
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_iters} ITA iteration(s) of the same 8192x8192 workload from "
-                         f"X=0 (numpy/scipy complex128, scipy.fft workers={cores}); echo built by "
-                         "the oracle's own G"}
+                         f"X=0 (numpy/scipy complex128, scipy.fft workers={cores}, elementwise "
+                         "numpy on one thread); echo built by the oracle's own G"}
+        cpu1 = {"value": 1.0 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the same {args.cpu_iters} iteration(s) with scipy.fft workers=1"}
 
     # kernels of one fixed-step iteration (direct sparse DFT, sparse-FFT path, R1, C2, R2,
     # C3, check, 3 x (round, pick), count, scan, scatter, finish; the re-passes are
@@ -517,7 +581,8 @@ def main():
                        "l2": "no flush: every array (512 MiB) exceeds the 129 MB L2",
                        "parallelism": f"independent scenes x{world}"},
             "roofline": roofline, "passes": passes, "clocks": clocks, "e2e": e2e,
-            "gpu_launches": kernels_per_iter * args.steps + kernels_per_solve, "cpu_baseline": cpu}
+            "gpu_launches": kernels_per_iter * args.steps + kernels_per_solve, "cpu_baseline": cpu,
+            "cpu_baseline_1core": cpu1, "cufft_comparison": cmp}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

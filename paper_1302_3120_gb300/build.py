@@ -15,6 +15,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcsar.so")
+# cuFFT-based comparison build of the ITA iteration (timed by bench.py only; not part of
+# libcsar): compare/cufft_ita.cu -> libcsar_cufft.so, linked against libcsar and cuFFT
+CMP_SRC = os.path.join(HERE, "compare", "cufft_ita.cu")
+CMP_OUT = os.path.join(HERE, "libcsar_cufft.so")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -54,6 +58,28 @@ def needs_build() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def build_compare(force: bool = False) -> str | None:
+    """libcsar_cufft.so (the benchmark's cuFFT comparison build); None if it cannot be
+    built (the benchmark then reports the comparison as unavailable)."""
+    if (not force and os.path.exists(CMP_OUT) and os.path.getmtime(CMP_OUT) >= os.path.getmtime(CMP_SRC)
+            and os.path.getmtime(CMP_OUT) >= os.path.getmtime(OUT)):
+        return CMP_OUT
+    os.makedirs(BUILD, exist_ok=True)
+    obj = os.path.join(BUILD, "cufft_ita.o")
+    r = subprocess.run([nvcc(), *ARCH, *FLAGS, "-c", CMP_SRC, "-o", obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(f"cuFFT comparison build skipped (compile):\n{r.stderr}\n")
+        return None
+    tmp = CMP_OUT + ".tmp"
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, obj, "-L" + HERE, "-lcsar", "-lcufft",
+                        "-lcudart", "-Xlinker", "-rpath=$ORIGIN"], capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(f"cuFFT comparison build skipped (link):\n{r.stderr}\n")
+        return None
+    os.replace(tmp, CMP_OUT)
+    return CMP_OUT
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return OUT
@@ -67,6 +93,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, OUT)
+    build_compare(force=True)
     return OUT
 
 
