@@ -87,6 +87,15 @@ typedef struct csar_batch_s* csar_batch;
 #define CSAR_PLAN_COL_CLUSTER(p) ((uint32_t)(p) << 8)
 #define CSAR_PLAN_COL_HALF_TILE ((uint32_t)1 << 16)
 #define CSAR_PLAN_COL_WIDE_TILE ((uint32_t)1 << 18)
+/* csar_plan_create flags: CSAR_PLAN_COL_PERSIST runs the forward, inverse, residue and
+ * selection column passes as persistent clusters that walk the column tiles, each
+ * tile's block arriving by 2-D tensor copies into a landing buffer while the previous
+ * tile is transformed (alone: clusters of n_az/1024 CTAs of 4096 values, n_az >= 1024;
+ * with the cluster / tile flags above: that configuration, if built persistent).
+ * CSAR_PLAN_COL_NO_PERSIST keeps the per-tile column kernels whatever the default or
+ * the autotuner chose.  Results are the same either way; only speed differs. */
+#define CSAR_PLAN_COL_PERSIST ((uint32_t)1 << 19)
+#define CSAR_PLAN_COL_NO_PERSIST ((uint32_t)1 << 20)
 
 /* csar_plan_create flag: csar_G / csar_M use the range-Doppler operator pair of the
  * paper's concrete example (Section III-C, Eqs. (14)-(18)) instead of the chirp-scaling

@@ -511,3 +511,6 @@ PLAN_COL_HALF_TILE = 1 << 16
 PLAN_COL_WIDE_TILE = 1 << 18
 # csar_plan_create flag: G / M are the range-Doppler operator pair with sinc RCMC
 PLAN_RDA = 1 << 17
+# csar_plan_create flags: persistent, tensor-copy-fed column passes, or never
+PLAN_COL_PERSIST = 1 << 19
+PLAN_COL_NO_PERSIST = 1 << 20

@@ -889,8 +889,11 @@ int32_t csar_version(void) { return 10000; }
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
-  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_RDA))
+  if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_RDA |
+                CSAR_PLAN_COL_PERSIST | CSAR_PLAN_COL_NO_PERSIST))
     return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
+  if ((flags & CSAR_PLAN_COL_PERSIST) && (flags & CSAR_PLAN_COL_NO_PERSIST))
+    return fail(CSAR_E_INVALID, "CSAR_PLAN_COL_PERSIST with CSAR_PLAN_COL_NO_PERSIST");
   const uint32_t tile_flags = flags & (CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE);
   if (tile_flags == (CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE))
     return fail(CSAR_E_UNSUPPORTED, "half and wide column tiles together");
@@ -899,11 +902,17 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   forced.p = forced_p;
   forced.e = (flags & CSAR_PLAN_COL_HALF_TILE) ? kColCtaElems / 2
                                                : ((flags & CSAR_PLAN_COL_WIDE_TILE) ? 2 * kColCtaElems : kColCtaElems);
+  const bool persist = (flags & CSAR_PLAN_COL_PERSIST) != 0;
   if ((forced_p || tile_flags) && params) {
     if (!forced_p) forced.p = col_conf_default(params->n_az).p;
+    forced.persist = persist;
     if (!col_conf_ok(params->n_az, forced))
-      return fail(CSAR_E_UNSUPPORTED, "column configuration (cluster %d, %d values per CTA) not available "
-                  "for n_az=%d", forced.p, forced.e, params->n_az);
+      return fail(CSAR_E_UNSUPPORTED, "column configuration (cluster %d, %d values per CTA%s) not available "
+                  "for n_az=%d", forced.p, forced.e, persist ? ", persistent" : "", params->n_az);
+  } else if (persist && params) {
+    forced = col_conf_persist(params->n_az);
+    if (!col_conf_ok(params->n_az, forced))
+      return fail(CSAR_E_UNSUPPORTED, "persistent column passes not available for n_az=%d", params->n_az);
   }
   if (csar_status st = validate(params)) return st;
   std::vector<RowCoef> cg(params->n_az), cm(params->n_az);
@@ -925,12 +934,13 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->na = params->n_az;
   plan->nr = params->n_rg;
   plan->n = (int64_t)plan->na * plan->nr;
-  if (forced_p || tile_flags) {
+  if (forced_p || tile_flags || persist) {
     plan->col = plan->col_res = forced;
   } else if (!tuned_conf(plan->na, plan->nr, &plan->col, &plan->col_res)) {
     plan->col = col_conf_default(plan->na);
     plan->col_res = col_conf_default_res(plan->na);
   }
+  if (flags & CSAR_PLAN_COL_NO_PERSIST) plan->col.persist = plan->col_res.persist = false;
   // both configurations bucket the sparse iterate by the same tile width
   if (col_w(plan->na, plan->col_res.p, plan->col_res.e) != col_w(plan->na, plan->col.p, plan->col.e))
     plan->col_res = plan->col;

@@ -173,6 +173,8 @@ constexpr int kColCtaElems = 8192;   // default complex64 values per column-pass
 struct ColConf {
   int p = 1;                 // CTAs per cluster
   int e = kColCtaElems;      // complex64 values per CTA
+  bool persist = false;      // persistent clusters fed by tensor copies (colp_pass.cuh) for
+                             // the forward, inverse, residue and selection passes
 };
 __host__ __device__ constexpr int col_w(int n, int p, int e = kColCtaElems) {
   return e * p / n > 16 ? 16 : (e * p / n < 1 ? 1 : e * p / n);
@@ -202,6 +204,7 @@ csar_status set_error(csar_status st, const char* msg);
 bool col_conf_ok(int na, ColConf c);
 ColConf col_conf_default(int na);
 ColConf col_conf_default_res(int na);   // residue / NIHT-norm passes (same W as the default)
+ColConf col_conf_persist(int na);       // persistent passes: clusters of N_a/1024 CTAs of 4096 values
 cudaError_t launch_col(int na, ColConf conf, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);

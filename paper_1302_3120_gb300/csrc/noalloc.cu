@@ -77,7 +77,8 @@ extern "C" csar_status csar_G_noalloc(const csar_params* params, const void* x_d
     su.ptr = (unsigned char*)p;
     su.ready = true;
   }
-  const ColConf conf = col_conf_default(na);
+  ColConf conf = col_conf_default(na);
+  conf.persist = false;   // the per-tile column kernels: no tensor maps, no occupancy queries
   bool& cd = su.col_done[log2i(na)][log2i(conf.p)][conf.e == kColCtaElems ? 0 : 1];
   if (!cd) {
     if (col_set_attributes(na, conf) != cudaSuccess)
