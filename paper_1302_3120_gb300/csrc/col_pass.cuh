@@ -288,11 +288,19 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
     // F_a(S.g): the residue F_a r = F_a(S.Y) - F_a(S.g) is formed by the next range pass
     // as it loads its rows (contiguous reads there, where the pass hides their latency)
     bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
-    fft<Q, true, L, true, R>(v, sm, tw, t, w);
+    // the local inverse transform runs as the forward one of the conjugate (unnormalised
+    // IFFT(u) = conj(FFT(conj(u))), exact), so one copy of the FFT code serves both
+    // transforms in a rolled loop
 #pragma unroll
-    for (int s = 0; s < R; ++s)
-      v[s] = ((mbits >> s) & 1u) ? cscale(v[s], a.scale) : make_float2(0.f, 0.f);
-    fft<Q, false, L, true, R>(v, sm, tw, t, w);
+    for (int s = 0; s < R; ++s) v[s].y = -v[s].y;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      fft<Q, false, L, true, R>(v, sm, tw, t, w);
+      if (pass == 1) break;
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        v[s] = ((mbits >> s) & 1u) ? make_float2(v[s].x * a.scale, -v[s].y * a.scale) : make_float2(0.f, 0.f);
+    }
     if constexpr (P == 1) {
 #pragma unroll
       for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)(t + s * QR) * nr + col], v[s]);

@@ -137,18 +137,29 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
     const PhaseCoef c = cp->pro;
     phase_ap<R, 0, R>(v, c, t - N / 2, QR, 1.f, phase_second_diff(c, QR));
   }
-  fft<N, false, L, false>(v, sm, tw, t, w);
-  // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
-  if constexpr (kRowChains<N>) {
-    phase_chain<R, 0, R / 2>(v, cp->mid, t, QR, 1.f, gw + R);
-    phase_chain<R, R / 2, R>(v, cp->mid, t - (R / 2) * QR, QR, 1.f, gw + R);
-  } else {
-    const PhaseCoef c = cp->mid;
-    const float2 dd = phase_second_diff(c, QR);
-    phase_ap<R, 0, R / 2>(v, c, t, QR, 1.f, dd);
-    phase_ap<R, R / 2, R>(v, c, t - (R / 2) * QR, QR, 1.f, dd);
+  // The range IFFT runs as the forward FFT of the conjugate (unnormalised IFFT(u) =
+  // conj(FFT(conj(u))); conjugation commutes exactly with every rounded operation, so
+  // the result is the same), which lets one copy of the FFT code serve both transforms
+  // in a rolled loop: half the instruction footprint of two unrolled transforms.
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    fft<N, false, L, false>(v, sm, tw, t, w);
+    if (pass == 1) break;
+    // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
+    if constexpr (kRowChains<N>) {
+      phase_chain<R, 0, R / 2>(v, cp->mid, t, QR, 1.f, gw + R);
+      phase_chain<R, R / 2, R>(v, cp->mid, t - (R / 2) * QR, QR, 1.f, gw + R);
+    } else {
+      const PhaseCoef c = cp->mid;
+      const float2 dd = phase_second_diff(c, QR);
+      phase_ap<R, 0, R / 2>(v, c, t, QR, 1.f, dd);
+      phase_ap<R, R / 2, R>(v, c, t - (R / 2) * QR, QR, 1.f, dd);
+    }
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s].y = -v[s].y;
   }
-  fft<N, true, L, false>(v, sm, tw, t, w);
+#pragma unroll
+  for (int s = 0; s < R; ++s) v[s].y = -v[s].y;
   if constexpr (kRowChains<N>) {
     phase_chain<R, 0, R>(v, cp->epi, t - N / 2, QR, a.scale, gw + 2 * R);
   } else {
