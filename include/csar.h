@@ -194,6 +194,20 @@ csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t
                                void* X_dev, const csar_opts* opts, float* pass_ms,
                                int32_t n_pass, void* stream);
 
+/* Non-chirp pulse (Section III-D, second generalisation: the approximated observation
+ * applies to any transmitted pulse once the range matched filter's conjugate P_tau^* is
+ * replaced by the recorded pulse).  On a CSAR_PLAN_RDA plan, spectrum_host (2 * n_rg
+ * floats: re, im of the transmitted pulse's range spectrum S at every range-frequency
+ * bin, FFT order: bin j is frequency j fs / n_rg for j < n_rg/2 and (j - n_rg) fs / n_rg
+ * above; the pulse's time origin, where its compressed peak falls, at delay 0) replaces
+ * the chirp filter from then on: G multiplies the range spectrum by S, M by conj(S), so
+ * G = M^H still holds (Theorem 1), while M G = I only for a unit-modulus S.  NULL
+ * restores the chirp filter exp(j pi f^2 / K_r).  The table is copied; the call
+ * synchronises the device and drops the plan's captured graphs.  CSAR_E_UNSUPPORTED on
+ * a chirp-scaling plan (chirp scaling is defined for linear FM pulses only),
+ * CSAR_E_INVALID for a non-finite entry. */
+csar_status csar_plan_set_pulse(csar_plan plan, const float* spectrum_host);
+
 /* ---- Differentiable autofocus (per-pulse azimuth phase error theta) ----------------
  * Observation A_theta X = S . (exp(j theta_eta) . G(X)) with one real phase theta_eta
  * per echo row (pulse).  Its ITA is Algorithm 1 on the de-rotated echo

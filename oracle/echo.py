@@ -23,9 +23,12 @@ import numpy as np
 from . import csa
 
 
-def point_echo(g, rows, cols, amps) -> np.ndarray:
+def point_echo(g, rows, cols, amps, pulse=None) -> np.ndarray:
     """Raw echo [N_a, N_r] of point targets placed on image pixels (row, col):
-    eta_t = eta_grid[row], R_t = R0(tau_grid[col])."""
+    eta_t = eta_grid[row], R_t = R0(tau_grid[col]).  ``pulse``: a baseband transmitted
+    pulse p(t) (callable, t from the pulse's time origin, zero outside its support) in
+    place of the up-chirp rect(t/T_p) exp(j pi K_r t^2) (Section III-D, non-chirp
+    pulses)."""
     c = csa._c(g)
     eta = csa.eta_grid(g)[:, None]
     tau = csa.tau_grid(g)[None, :]
@@ -38,9 +41,13 @@ def point_echo(g, rows, cols, amps) -> np.ndarray:
         t_a = 0.886 * g.wavelength * r_t / (g.antenna_len * g.velocity)
         r = np.sqrt(r_t ** 2 + (g.velocity * (eta - eta_t)) ** 2)
         delay = tau - 2.0 * r / c
-        env = (np.abs(delay) <= g.pulse_len / 2) & (np.abs(eta - eta_t) <= t_a / 2)
-        ph = -4.0 * np.pi * fc * r / c + np.pi * kr * delay ** 2
-        out += np.where(env, a * np.exp(1j * ph), 0.0)
+        in_beam = np.abs(eta - eta_t) <= t_a / 2
+        if pulse is None:
+            env = (np.abs(delay) <= g.pulse_len / 2) & in_beam
+            ph = -4.0 * np.pi * fc * r / c + np.pi * kr * delay ** 2
+            out += np.where(env, a * np.exp(1j * ph), 0.0)
+        else:
+            out += np.where(in_beam, a * np.exp(-4j * np.pi * fc * r / c) * pulse(delay), 0.0)
     return out
 
 

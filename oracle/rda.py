@@ -36,9 +36,24 @@ TAP_LO = N_TAPS // 2 - 1
 
 
 def range_filter(g) -> np.ndarray:
-    """P_tau(f_tau) = exp(j pi f_tau^2 / K_r), one value per range-frequency bin."""
+    """P_tau(f_tau) = exp(j pi f_tau^2 / K_r), one value per range-frequency bin.  For a
+    recorded (non-chirp) transmitted pulse (Section III-D, second generalisation: P_tau^*
+    is replaced by the transmitted pulse), ``g.pulse`` holds the pulse's range spectrum S
+    (``pulse_spectrum``), G multiplies by S and M by P_tau = conj(S)."""
+    s = getattr(g, "pulse", None)
+    if s is not None:
+        return np.conj(np.asarray(s, dtype=np.complex128))
     ft = csa.f_tau_grid(g)
     return np.exp(1j * np.pi * ft ** 2 / csa.k_r(g))
+
+
+def pulse_spectrum(g, pulse) -> np.ndarray:
+    """Range spectrum S of a baseband pulse p(t) (a callable, t in seconds from the
+    pulse's time origin, zero outside its support) on the circular range grid:
+    S[j] = sum_n p(t_n) exp(-j 2 pi j n / N_r), t_n = n / fs for the signed sample index
+    n (FFT order), so that the compressed peak of an echo p(tau - 2R/c) lies at 2R/c."""
+    n = np.fft.fftfreq(g.n_rg, d=1.0 / g.n_rg)
+    return np.fft.fft(pulse(n / g.fs))
 
 
 def azimuth_filter(g) -> np.ndarray:

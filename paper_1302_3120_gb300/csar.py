@@ -56,7 +56,7 @@ EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_it
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
            "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
            "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout", "csar_echo_points",
-           "csar_debug_selection_enable", "csar_debug_selection_read")
+           "csar_debug_selection_enable", "csar_debug_selection_read", "csar_plan_set_pulse")
 
 
 def _load() -> ctypes.CDLL:
@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
     lib.csar_autotune.argtypes = [ctypes.POINTER(Params), i32, ctypes.POINTER(i32)]
     lib.csar_selftest_wait_timeout.argtypes = [i32]
     lib.csar_echo_points.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int64, vp, i32, vp]
+    lib.csar_plan_set_pulse.argtypes = [vp, vp]
     lib.csar_debug_selection_enable.argtypes = [vp, ctypes.c_int64]
     lib.csar_debug_selection_read.argtypes = [vp, vp, vp, vp, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(u32),
@@ -99,7 +100,7 @@ def _load() -> ctypes.CDLL:
                  "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc",
                  "csar_batch_create", "csar_batch_destroy", "csar_solve_batched", "csar_batch_check",
                  "csar_autotune", "csar_echo_points", "csar_debug_selection_enable",
-                 "csar_debug_selection_read"):
+                 "csar_debug_selection_read", "csar_plan_set_pulse"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -305,6 +306,18 @@ def csar_solve_profile(plan: Plan, Y, mask_bits, K: int, iters: int, mu_mode="fi
 
 def csar_plan_check(plan: Plan) -> None:
     _check(lib.csar_plan_check(plan.handle), "csar_plan_check")
+
+
+def csar_plan_set_pulse(plan: Plan, spectrum=None) -> None:
+    """Range spectrum of a recorded (non-chirp) transmitted pulse for a range-Doppler
+    plan, n_rg complex values in FFT bin order (None: back to the chirp filter)."""
+    if spectrum is None:
+        _check(lib.csar_plan_set_pulse(plan.handle, None), "csar_plan_set_pulse")
+        return
+    s = np.ascontiguousarray(np.asarray(spectrum).astype(np.complex64).reshape(-1))
+    if s.size != plan.n_rg:
+        raise ValueError(f"pulse spectrum needs {plan.n_rg} bins, got {s.size}")
+    _check(lib.csar_plan_set_pulse(plan.handle, ctypes.c_void_p(s.ctypes.data)), "csar_plan_set_pulse")
 
 
 def csar_debug_selection_enable(plan: Plan, capacity: int) -> None:

@@ -320,6 +320,8 @@ struct csar_plan_s {
   bool rda = false;
   RowCoef* rda_rg_g = nullptr;
   RowCoef* rda_rg_m = nullptr;
+  float2* rda_pulse_g = nullptr;  // recorded pulse spectrum S (G) and conj(S) (M), if set
+  float2* rda_pulse_m = nullptr;
   RcmcCoef* rda_rcmc = nullptr;
   float2* tw = nullptr;
   Buffers b;
@@ -447,6 +449,7 @@ cudaError_t range_pass(csar_plan plan, const RowArgs& r, bool is_g, cudaStream_t
   a.data = r.data;
   a.rc = plan->rda_rcmc + (is_g ? plan->na : 0);
   a.rg = is_g ? plan->rda_rg_g : plan->rda_rg_m;
+  a.rtab = is_g ? plan->rda_pulse_g : plan->rda_pulse_m;
   a.tw = r.tw;
   a.gate = r.gate;
   a.gate_val = r.gate_val;
@@ -1029,6 +1032,8 @@ csar_status csar_plan_destroy(csar_plan plan) {
   if (plan->coef_m) cudaFree(plan->coef_m);
   if (plan->rda_rg_g) cudaFree(plan->rda_rg_g);
   if (plan->rda_rg_m) cudaFree(plan->rda_rg_m);
+  if (plan->rda_pulse_g) cudaFree(plan->rda_pulse_g);
+  if (plan->rda_pulse_m) cudaFree(plan->rda_pulse_m);
   if (plan->rda_rcmc) cudaFree(plan->rda_rcmc);
   if (plan->tw) cudaFree(plan->tw);
   delete plan;
@@ -1102,6 +1107,50 @@ csar_status csar_plan_check(csar_plan plan) {
   DeviceGuard dg(plan->dev);
   CK(cudaDeviceSynchronize());
   return latched(plan);
+}
+
+csar_status csar_plan_set_pulse(csar_plan plan, const float* spectrum_host) {
+  if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
+  if (!plan->rda)
+    return fail(CSAR_E_UNSUPPORTED, "a recorded pulse replaces the range filter of the range-Doppler "
+                "pair; chirp scaling assumes a linear FM pulse");
+  const int nr = plan->nr;
+  std::vector<float2> sg, sm;
+  if (spectrum_host) {
+    sg.resize(nr);
+    sm.resize(nr);
+    for (int j = 0; j < nr; ++j) {
+      const float re = spectrum_host[2 * j], im = spectrum_host[2 * j + 1];
+      if (!std::isfinite(re) || !std::isfinite(im)) return fail(CSAR_E_INVALID, "pulse spectrum bin %d is not finite", j);
+      sg[j] = make_float2(re, im);
+      sm[j] = make_float2(re, -im);
+    }
+  }
+  DeviceGuard dg(plan->dev);
+  CK(cudaDeviceSynchronize());
+  drop_graphs(plan);
+  if (!spectrum_host) {
+    if (plan->rda_pulse_g) cudaFree(plan->rda_pulse_g);
+    if (plan->rda_pulse_m) cudaFree(plan->rda_pulse_m);
+    plan->rda_pulse_g = plan->rda_pulse_m = nullptr;
+    return CSAR_OK;
+  }
+  if (!plan->rda_pulse_g) {
+    float2* g = nullptr;
+    float2* m = nullptr;
+    cudaError_t e = dalloc(&g, (size_t)nr);
+    if (e == cudaSuccess) e = dalloc(&m, (size_t)nr);
+    if (e != cudaSuccess) {
+      if (g) cudaFree(g);
+      if (m) cudaFree(m);
+      return fail(CSAR_E_OOM, "pulse spectrum: %s", cudaGetErrorString(e));
+    }
+    plan->rda_pulse_g = g;
+    plan->rda_pulse_m = m;
+  }
+  CK(cudaMemcpy(plan->rda_pulse_g, sg.data(), nr * sizeof(float2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan->rda_pulse_m, sm.data(), nr * sizeof(float2), cudaMemcpyHostToDevice));
+  return CSAR_OK;
 }
 
 csar_status csar_debug_selection_enable(csar_plan plan, int64_t capacity) {

@@ -154,6 +154,8 @@ struct RdaArgs {
   float2* data;
   const RcmcCoef* rc;    // migration and azimuth filter, one per row
   const RowCoef* rg;     // range filter P_tau (or its conjugate) as the middle phase
+  const float2* rtab;    // if non-null: the range filter as a table over the N_r range-
+                         // frequency bins in FFT order (non-chirp pulse), instead of rg
   const float2* tw;
   const uint32_t* gate;
   uint32_t gate_val;

@@ -257,7 +257,12 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row_rda(RdaArgs a) {
   // range compression: FFT, x P_tau (or conj), IFFT / N_r; range-frequency bin of v[s]
   // is t + s QR for s < R/2 and t + (s - R) QR above
   fft<N, false, L, false>(v, sm, tw, t, w);
-  if constexpr (kRdaChains<N>) {
+  if (a.rtab) {
+    // a recorded pulse (Section III-D): the filter is a table over the range-frequency
+    // bins, FFT order, so v[s] (bin t + s QR modulo N) takes entry t + s QR
+#pragma unroll
+    for (int s = 0; s < R; ++s) v[s] = cmul(v[s], __ldg(&a.rtab[t + s * QR]));
+  } else if constexpr (kRdaChains<N>) {
     phase_chain<R, 0, R / 2>(v, mid, t, QR, 1.f, gw);
     phase_chain<R, R / 2, R>(v, mid, t - (R / 2) * QR, QR, 1.f, gw);
   } else {

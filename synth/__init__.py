@@ -171,3 +171,22 @@ def batch_shapes(rng: np.random.Generator, count: int = 64,
     a = rng.choice(sizes, size=count)
     r = rng.choice(sizes, size=count)
     return [(int(x), int(y)) for x, y in zip(a, r)]
+
+
+# ----------------------------------------------------------------------------- pulses
+
+BARKER13 = np.array([1, 1, 1, 1, 1, -1, -1, 1, 1, -1, 1, -1, 1], dtype=np.float64)
+
+
+def coded_pulse(code, chip: float):
+    """Baseband phase-coded pulse p(t): chip k (duration ``chip`` seconds) carries
+    code[k]; the chips span [-len(code) chip / 2, len(code) chip / 2) around the pulse's
+    time origin; zero outside.  Returns a callable of t (seconds, array)."""
+    code = np.asarray(code)
+    n = len(code)
+
+    def p(t):
+        k = np.floor(np.asarray(t) / chip + n / 2.0).astype(np.int64)
+        inside = (k >= 0) & (k < n)
+        return np.where(inside, code[np.clip(k, 0, n - 1)], 0).astype(np.complex128)
+    return p

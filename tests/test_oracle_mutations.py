@@ -175,3 +175,32 @@ def test_echo_mutation_is_caught(name, monkeypatch):
     attr, fn = ECHO_MUTATIONS[name]
     monkeypatch.setattr(echo, attr, fn)
     assert _some_pin_fails(ECHO_PINS), name
+
+
+import test_oracle_pulse as pulse_pins  # noqa: E402
+from oracle import rda  # noqa: E402
+
+PULSE_PINS = [pulse_pins.test_pulse_spectrum_of_delayed_impulses,
+              pulse_pins.test_chirp_spectrum_reduces_to_the_chirp_filter,
+              pulse_pins.test_barker_coded_point_targets_focus]
+_range_filter, _pulse_spectrum = rda.range_filter, rda.pulse_spectrum
+
+
+def _rf_unconjugated(g):
+    s = getattr(g, "pulse", None)
+    return np.asarray(s, complex) if s is not None else _range_filter(g)
+
+
+PULSE_MUTATIONS = {
+    "recorded pulse not conjugated in M": ("range_filter", _rf_unconjugated),
+    "pulse spectrum time-reversed": ("pulse_spectrum", lambda g, p: _pulse_spectrum(g, lambda t: p(-t))),
+    "pulse spectrum by inverse DFT": (
+        "pulse_spectrum", lambda g, p: g.n_rg * np.fft.ifft(p(np.fft.fftfreq(g.n_rg, 1.0 / g.n_rg) / g.fs))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PULSE_MUTATIONS))
+def test_pulse_mutation_is_caught(name, monkeypatch):
+    attr, fn = PULSE_MUTATIONS[name]
+    monkeypatch.setattr(rda, attr, fn)
+    assert _some_pin_fails(PULSE_PINS), name
