@@ -328,6 +328,16 @@ csar_status csar_debug_selection_read(csar_plan plan, uint32_t* idx_host, float*
                                       uint32_t* key_host, int64_t capacity, int64_t* count,
                                       uint32_t* sigma2_key, float* mu, float* sigma);
 
+/* ---- Test hook of the out-of-memory paths (host-side fault injection) ------------
+ * After csar_debug_fail_alloc(n) with n > 0, the n-th device allocation the library
+ * makes from then on (plans, workspaces grown on demand, host-buffer staging, records)
+ * fails as if the device were out of memory, without allocating: the entry point that
+ * made it returns CSAR_E_OOM and frees what it had allocated for the call.  n = 0 turns
+ * the injection off.  Process-wide; not thread-safe against concurrent allocations.
+ * The paper has no counterpart: it lets tests drive every allocation-failure path
+ * without touching the GPU's memory state. */
+csar_status csar_debug_fail_alloc(int32_t n);
+
 /* Synchronise the plan's device and report (and clear) any latched device-side
  * error of the plan (CSAR_E_NONFINITE, CSAR_E_INTERNAL, CSAR_E_TIMEOUT, ...). */
 csar_status csar_plan_check(csar_plan plan);

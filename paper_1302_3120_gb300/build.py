@@ -17,6 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcsar.so")
 # cuFFT-based comparison build of the ITA iteration (timed by bench.py only; not part of
 # libcsar): compare/cufft_ita.cu -> libcsar_cufft.so, linked against libcsar and cuFFT
+CHECKED_OUT = os.path.join(HERE, "libcsar_checked.so")
 CMP_SRC = os.path.join(HERE, "compare", "cufft_ita.cu")
 CMP_OUT = os.path.join(HERE, "libcsar_cufft.so")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
@@ -36,9 +37,9 @@ def sources() -> list[str]:
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cu"))
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose: bool, extra=(), bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -80,21 +81,33 @@ def build_compare(force: bool = False) -> str | None:
     return CMP_OUT
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
+def build_checked() -> str:
+    """libcsar_checked.so: the same library compiled with -DCSAR_CHECKED (global
+    indexes of the pass kernels compared with their arrays' extents; an index out of
+    range is skipped and reported as CSAR_E_INTERNAL).  Load it by setting
+    CSAR_LIB_PATH before importing the binding."""
+    return build(force=True, checked=True)
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out = CHECKED_OUT if checked else OUT
+    if not checked and not force and not needs_build():
         return OUT
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD + ("_checked" if checked else "")
+    os.makedirs(bdir, exist_ok=True)
     srcs = sources()
+    extra = ["-DCSAR_CHECKED"] if checked else []
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = OUT + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, extra, bdir), srcs))
+    tmp = out + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    build_compare(force=True)
-    return OUT
+    os.replace(tmp, out)
+    if not checked:
+        build_compare(force=True)
+    return out
 
 
 if __name__ == "__main__":

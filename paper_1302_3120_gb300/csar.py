@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcsar.so")
+# CSAR_LIB_PATH selects another build of the library (the checked build,
+# libcsar_checked.so); by default the in-tree libcsar.so
+LIB_PATH = os.environ.get("CSAR_LIB_PATH") or os.path.join(_HERE, "libcsar.so")
 
 CSAR_OK = 0
 STATUS_NAMES = {0: "CSAR_OK", 1: "CSAR_E_INVALID", 2: "CSAR_E_UNSUPPORTED", 3: "CSAR_E_OOM",
@@ -56,7 +58,8 @@ EXPORTS = ("csar_plan_create", "csar_plan_destroy", "csar_G", "csar_M", "csar_it
            "csar_last_error", "csar_version", "csar_af_solve", "csar_af_loss", "csar_af_backward",
            "csar_G_noalloc", "csar_batch_create", "csar_batch_destroy", "csar_solve_batched",
            "csar_batch_check", "csar_autotune", "csar_selftest_wait_timeout", "csar_echo_points",
-           "csar_debug_selection_enable", "csar_debug_selection_read", "csar_plan_set_pulse")
+           "csar_debug_selection_enable", "csar_debug_selection_read", "csar_plan_set_pulse",
+           "csar_debug_fail_alloc")
 
 
 def _load() -> ctypes.CDLL:
@@ -88,6 +91,7 @@ def _load() -> ctypes.CDLL:
     lib.csar_selftest_wait_timeout.argtypes = [i32]
     lib.csar_echo_points.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int64, vp, i32, vp]
     lib.csar_plan_set_pulse.argtypes = [vp, vp]
+    lib.csar_debug_fail_alloc.argtypes = [i32]
     lib.csar_debug_selection_enable.argtypes = [vp, ctypes.c_int64]
     lib.csar_debug_selection_read.argtypes = [vp, vp, vp, vp, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(u32),
@@ -100,7 +104,7 @@ def _load() -> ctypes.CDLL:
                  "csar_af_solve", "csar_af_loss", "csar_af_backward", "csar_G_noalloc",
                  "csar_batch_create", "csar_batch_destroy", "csar_solve_batched", "csar_batch_check",
                  "csar_autotune", "csar_echo_points", "csar_debug_selection_enable",
-                 "csar_debug_selection_read", "csar_plan_set_pulse"):
+                 "csar_debug_selection_read", "csar_plan_set_pulse", "csar_debug_fail_alloc"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -318,6 +322,12 @@ def csar_plan_set_pulse(plan: Plan, spectrum=None) -> None:
     if s.size != plan.n_rg:
         raise ValueError(f"pulse spectrum needs {plan.n_rg} bins, got {s.size}")
     _check(lib.csar_plan_set_pulse(plan.handle, ctypes.c_void_p(s.ctypes.data)), "csar_plan_set_pulse")
+
+
+def csar_debug_fail_alloc(n: int) -> None:
+    """Make the n-th device allocation of the library from now on fail as out of memory
+    (0: off)."""
+    _check(lib.csar_debug_fail_alloc(int(n)), "csar_debug_fail_alloc")
 
 
 def csar_debug_selection_enable(plan: Plan, capacity: int) -> None:

@@ -210,7 +210,10 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
   // sampling bits of this thread's R rows (pre-transposed: bit s <-> strided row s),
   // fetched first so the load is long complete when the mask is applied
   uint32_t mbits = 0u;
-  if constexpr (MODE == COL_RESID || MODE == COL_NORM) mbits = __ldg(&a.mask[((size_t)col * P + c) * QR + t]);
+  if constexpr (MODE == COL_RESID || MODE == COL_NORM) {
+    const size_t mi = ((size_t)col * P + c) * QR + t;
+    if (CSAR_CHECK(mi, (size_t)a.nr * (N / R), a.ctl)) mbits = __ldg(&a.mask[mi]);
+  }
   // exchange mbarriers, then every CTA of the cluster is running (and its mbarriers are
   // initialised) before any remote store or arrive
   const uint32_t mb0 = smem_addr(mbar);
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
         const int loc = (P == 1) ? row : (n2 - c * (Q / P));
         const int tt = loc % QR, i = loc / QR;
         const int s = (P == 1) ? i : i * P + n1;
-        sm[L::template at<4>(ww, tt + QR * s)] = a.xs_val[e];
+        if (CSAR_CHECK(ww, W, a.ctl)) sm[L::template at<4>(ww, tt + QR * s)] = a.xs_val[e];
       }
     }
     __syncthreads();
@@ -260,7 +263,10 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
     }
   } else {
 #pragma unroll
-    for (int s = 0; s < R; ++s) v[s] = __ldcs(&a.in[(size_t)bs_in_row<N, P, E>(c, t, s) * nr + col]);
+    for (int s = 0; s < R; ++s) {
+      const size_t gi = (size_t)bs_in_row<N, P, E>(c, t, s) * nr + col;
+      v[s] = CSAR_CHECK(gi, (size_t)N * nr, a.ctl) ? __ldcs(&a.in[gi]) : make_float2(0.f, 0.f);
+    }
   }
   // selection passes: the support range of this tile, its first entry per thread and the
   // candidate cut are fetched while the column loads are in flight
@@ -277,13 +283,18 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
     bs_cross<N, P, E, false>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, false, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
-    for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)strided_row<N, P, E>(c, t, s) * nr + col], v[s]);
+    for (int s = 0; s < R; ++s) {
+      const size_t gi = (size_t)strided_row<N, P, E>(c, t, s) * nr + col;
+      if (CSAR_CHECK(gi, (size_t)N * nr, a.ctl)) __stcs(&a.out[gi], v[s]);
+    }
   } else if constexpr (MODE == COL_INV) {
     bs_cross<N, P, E, true>(v, sm, tw, c, t, w, peer, mb0 + 8u * kMbBs, a.ctl);
     fft<Q, true, L, true, R>(v, sm, tw, t, w);
 #pragma unroll
-    for (int s = 0; s < R; ++s)
-      __stcs(&a.out[(size_t)strided_row<N, P, E>(c, t, s) * nr + col], cscale(v[s], a.scale));
+    for (int s = 0; s < R; ++s) {
+      const size_t gi = (size_t)strided_row<N, P, E>(c, t, s) * nr + col;
+      if (CSAR_CHECK(gi, (size_t)N * nr, a.ctl)) __stcs(&a.out[gi], cscale(v[s], a.scale));
+    }
   } else if constexpr (MODE == COL_RESID) {
     // F_a(S.g): the residue F_a r = F_a(S.Y) - F_a(S.g) is formed by the next range pass
     // as it loads its rows (contiguous reads there, where the pass hides their latency)
@@ -303,7 +314,10 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
     }
     if constexpr (P == 1) {
 #pragma unroll
-      for (int s = 0; s < R; ++s) __stcs(&a.out[(size_t)(t + s * QR) * nr + col], v[s]);
+      for (int s = 0; s < R; ++s) {
+        const size_t gi = (size_t)(t + s * QR) * nr + col;
+        if (CSAR_CHECK(gi, (size_t)N * nr, a.ctl)) __stcs(&a.out[gi], v[s]);
+      }
     } else {
       // SB step: twiddle W_N^(c k2) (k2 = t + s QR) and push k2 to CTA s / RP at element
       // c*Q/P + k2l (source-major, so pushes and the final reads are conflict-free), once
@@ -338,7 +352,10 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
         for (int n1 = 0; n1 < P; ++n1) b[n1] = sm[L::template at<4>(w, n1 * (Q / P) + k2l)];
         Dft<P, false>::run(b);
 #pragma unroll
-        for (int k1 = 0; k1 < P; ++k1) __stcs(oc + i * di + k1 * dk, b[k1]);
+        for (int k1 = 0; k1 < P; ++k1) {
+          const size_t gi = (size_t)(c * (Q / P) + t) * nr + col + i * di + k1 * dk;
+          if (CSAR_CHECK(gi, (size_t)N * nr, a.ctl)) __stcs(oc + i * di + k1 * dk, b[k1]);
+        }
       }
     }
   } else if constexpr (MODE == COL_NORM) {
@@ -379,6 +396,7 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
       if (P > 1 && row % P != c) continue;
       const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
       const int m = row / P;
+      if (!CSAR_CHECK(ww, W, a.ctl)) continue;
       atomicOr(&msk[(m % QR) * W + ww], 1u << (m / QR));
     }
     __syncthreads();
@@ -426,7 +444,8 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
         const int row = (int)(idx / (uint32_t)a.nr);
         if (P > 1 && row % P != c) continue;
         const int ww = (int)(idx % (uint32_t)a.nr) - tile * W;
-        a.xs_dx[e] = sm[L::template at<4>(ww, row / P)];
+        if (CSAR_CHECK(ww, W, a.ctl) && CSAR_CHECK(e, (size_t)N * nr, a.ctl))
+          a.xs_dx[e] = sm[L::template at<4>(ww, row / P)];
       }
     }
     if (hist_on) {

@@ -9,6 +9,9 @@
 // the selection, the NIHT branch) are taken on the device by kernels that return
 // early, so one graph serves every iteration.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
 
 #include <algorithm>
 #include <cmath>
@@ -363,10 +366,29 @@ struct DeviceGuard {
   }
 };
 
+// Allocation-failure injection (csar_debug_fail_alloc): the n-th device allocation
+// after the call reports cudaErrorMemoryAllocation without allocating.
+std::atomic<long> g_fail_alloc_at{0};
+std::atomic<long> g_alloc_count{0};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
+  const long at = g_fail_alloc_at.load();
+  if (at > 0 && g_alloc_count.fetch_add(1) + 1 == at) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
 }
+
+// NVTX ranges around the entry points and, outside graph capture, around each pass of
+// an iteration (no cost without an attached tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void free_buffers(Buffers& b) {
   void* ptrs[] = {b.z, b.off[0], b.off[1], b.idx[0], b.idx[1], b.val[0], b.val[1], b.dx, b.cand_idx,
@@ -555,7 +577,23 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   const uint32_t* mask = b.mask_t;
   const int na = plan->na, nr = plan->nr, nt = plan->n_tiles;
   const int nxt = 1 - cur;
-  auto mark = [&](int i) -> cudaError_t { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+  // per-pass NVTX ranges (host enqueue; outside capture only)
+  static const char* const kPassNames[kPasses] = {"C1 sparse azimuth FFT", "R1 range pass of G", "C2 residue",
+                                                  "R2 range pass of M", "C3 selection pass", "selection"};
+  struct PassRange {
+    bool on, open = false;
+    ~PassRange() {
+      if (open) nvtxRangePop();
+    }
+  } nvtx{!capturing(s)};
+  auto mark = [&](int i) -> cudaError_t {
+    if (nvtx.on) {
+      if (nvtx.open) nvtxRangePop();
+      nvtx.open = i < kPasses;
+      if (nvtx.open) nvtxRangePushA(kPassNames[i]);
+    }
+    return ev ? cudaEventRecord(ev[i], s) : cudaSuccess;
+  };
   ColArgs c = col_args(plan);
   c.xs_off = b.off[cur];
   c.xs_idx = b.idx[cur];
@@ -724,6 +762,7 @@ cudaError_t dense_op(csar_plan plan, const float2* in, float2* out, bool is_g, c
 }
 
 csar_status run_op(csar_plan plan, const void* in, void* out, bool is_g, void* stream) {
+  NvtxRange nvtx_(is_g ? "csar_G" : "csar_M");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (!in || !out) return fail(CSAR_E_INVALID, "null data pointer");
   const size_t bytes = (size_t)plan->n * sizeof(float2);
@@ -768,6 +807,8 @@ csar_status latched(csar_plan plan) {
       return fail(CSAR_E_INTERNAL, "selection candidate capacity exceeded (degenerate magnitudes)");
     if (c.err & kErrTimeout)
       return fail(CSAR_E_TIMEOUT, "a column-pass cluster exchange timed out (a peer CTA never signalled)");
+    if (c.err & kErrIndex)
+      return fail(CSAR_E_INTERNAL, "an index out of range was caught and skipped (checked build)");
     return fail(CSAR_E_INTERNAL, "device error bits 0x%x", c.err);
   }
   return CSAR_OK;
@@ -853,12 +894,23 @@ csar_status solve_impl(csar_plan plan, const void* Y, const uint32_t* mask, void
 csar_status ensure_af(csar_plan plan, int64_t K, int iters) {
   Buffers& b = plan->b;
   const size_t n = (size_t)plan->n;
-  if (!b.yt) {
-    CK(dalloc(&b.yt, n));
-    CK(dalloc(&b.af_xbar, n));
-    CK(dalloc(&b.af_bbar, n));
-    CK(dalloc(&b.af_h, n));
-    CK(dalloc(&b.row_loss, plan->na));
+  if (!b.yt || !b.af_xbar || !b.af_bbar || !b.af_h || !b.row_loss) {
+    // all or none: a failed allocation leaves none behind
+    cudaError_t e = b.yt ? cudaSuccess : dalloc(&b.yt, n);
+    if (e == cudaSuccess && !b.af_xbar) e = dalloc(&b.af_xbar, n);
+    if (e == cudaSuccess && !b.af_bbar) e = dalloc(&b.af_bbar, n);
+    if (e == cudaSuccess && !b.af_h) e = dalloc(&b.af_h, n);
+    if (e == cudaSuccess && !b.row_loss) e = dalloc(&b.row_loss, plan->na);
+    if (e != cudaSuccess) {
+      for (void* q : {(void*)b.yt, (void*)b.af_xbar, (void*)b.af_bbar, (void*)b.af_h, (void*)b.row_loss})
+        if (q) cudaFree(q);
+      b.yt = nullptr;
+      b.af_xbar = nullptr;
+      b.af_bbar = nullptr;
+      b.af_h = nullptr;
+      b.row_loss = nullptr;
+      return cuda_fail(e, "autofocus workspace");
+    }
   }
   const uint32_t cap = (uint32_t)std::min<int64_t>(plan->n, std::max<int64_t>(K, 1));
   if (iters > 0 && (b.ck_cap < cap || b.ck_iters_cap < iters)) {
@@ -890,6 +942,7 @@ const char* csar_last_error(void) { return g_last_error.c_str(); }
 int32_t csar_version(void) { return 10000; }
 
 csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_plan* out) {
+  NvtxRange nvtx_("csar_plan_create");
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_RDA |
@@ -1050,6 +1103,7 @@ csar_status csar_M(csar_plan plan, const void* y_dev, void* x_dev, void* stream)
 
 csar_status csar_ita_step(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
                           const csar_opts* opts, float* sigma_dev, void* stream) {
+  NvtxRange nvtx_("csar_ita_step");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (csar_status st = check_opts(plan, opts, false)) return st;
   if (!Y_dev || !mask_dev || !X_dev) return fail(CSAR_E_INVALID, "null data pointer");
@@ -1076,6 +1130,7 @@ csar_status csar_ita_step(csar_plan plan, const void* Y_dev, const uint32_t* mas
 
 csar_status csar_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
                        const csar_opts* opts, const csar_stats* stats, void* stream) {
+  NvtxRange nvtx_("csar_solve");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   DeviceGuard dg(plan->dev);
   return solve_impl(plan, Y_dev, mask_dev, X_dev, opts, stats, (cudaStream_t)stream);
@@ -1083,15 +1138,25 @@ csar_status csar_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_d
 
 csar_status csar_solve_host(csar_plan plan, const void* Y_host, const uint32_t* mask_host, void* X_host,
                             const csar_opts* opts, const csar_stats* stats, void* stream) {
+  NvtxRange nvtx_("csar_solve_host");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (!Y_host || !mask_host || !X_host) return fail(CSAR_E_INVALID, "null data pointer");
   DeviceGuard dg(plan->dev);
   Buffers& b = plan->b;
   const size_t n = (size_t)plan->n;
-  if (!b.hY) {
-    CK(dalloc(&b.hY, n));
-    CK(dalloc(&b.hMask, n / 32));
-    CK(dalloc(&b.hX, n));
+  if (!b.hY || !b.hMask || !b.hX) {
+    // all three or none: a failed allocation leaves none behind
+    cudaError_t e = b.hY ? cudaSuccess : dalloc(&b.hY, n);
+    if (e == cudaSuccess && !b.hMask) e = dalloc(&b.hMask, n / 32);
+    if (e == cudaSuccess && !b.hX) e = dalloc(&b.hX, n);
+    if (e != cudaSuccess) {
+      for (void* q : {(void*)b.hY, (void*)b.hMask, (void*)b.hX})
+        if (q) cudaFree(q);
+      b.hY = nullptr;
+      b.hMask = nullptr;
+      b.hX = nullptr;
+      return cuda_fail(e, "host-buffer staging");
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(b.hY, Y_host, n * sizeof(float2), cudaMemcpyHostToDevice, s));
@@ -1207,6 +1272,13 @@ csar_status csar_debug_selection_read(csar_plan plan, uint32_t* idx_host, float*
   return latched(plan);
 }
 
+csar_status csar_debug_fail_alloc(int32_t n) {
+  if (n < 0) return fail(CSAR_E_INVALID, "n must be >= 0");
+  g_alloc_count.store(0);
+  g_fail_alloc_at.store(n);
+  return CSAR_OK;
+}
+
 csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, void* X_dev,
                                const csar_opts* opts, float* pass_ms, int32_t n_pass, void* stream) {
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
@@ -1246,6 +1318,7 @@ csar_status csar_solve_profile(csar_plan plan, const void* Y_dev, const uint32_t
 
 csar_status csar_af_solve(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
                           void* X_dev, const csar_opts* opts, int32_t checkpoint, void* stream) {
+  NvtxRange nvtx_("csar_af_solve");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (!theta_dev) return fail(CSAR_E_INVALID, "theta is NULL");
   if (plan->rda) return fail(CSAR_E_UNSUPPORTED, "autofocus uses the chirp-scaling operator pair");
@@ -1289,6 +1362,7 @@ csar_status csar_af_loss(csar_plan plan, const void* Y_dev, const uint32_t* mask
 
 csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* mask_dev, const float* theta_dev,
                              const void* Xbar_dev, float* theta_bar_dev, void* X0bar_dev, void* stream) {
+  NvtxRange nvtx_("csar_af_backward");
   if (!plan) return fail(CSAR_E_INVALID, "plan is NULL");
   if (plan->rda) return fail(CSAR_E_UNSUPPORTED, "autofocus uses the chirp-scaling operator pair");
   if (!Y_dev || !mask_dev || !theta_dev || !Xbar_dev || !theta_bar_dev)
@@ -1370,6 +1444,7 @@ csar_status csar_batch_destroy(csar_batch b) {
 
 csar_status csar_solve_batched(csar_batch b, const void* const* Y_dev, const uint32_t* const* mask_dev,
                                void* const* X_dev, const int64_t* K, const csar_opts* opts, void* stream) {
+  NvtxRange nvtx_("csar_solve_batched");
   if (!b) return fail(CSAR_E_INVALID, "batch is NULL");
   if (!Y_dev || !mask_dev || !X_dev || !K || !opts) return fail(CSAR_E_INVALID, "null argument");
   const int np = (int)b->plans.size();

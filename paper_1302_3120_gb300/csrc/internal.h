@@ -33,7 +33,19 @@ enum : uint32_t {
 };
 
 // Device-latched error bits (reported by csar_plan_check).
-enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
+enum : uint32_t { kErrNonfinite = 1u, kErrCapacity = 2u, kErrTimeout = 4u, kErrIndex = 8u };
+
+// Checked build (compiled with -DCSAR_CHECKED): the global indexes of the pass kernels'
+// dense arrays and output lists are compared with the arrays' extents; an index out of
+// range latches kErrIndex (reported as CSAR_E_INTERNAL) and the access is skipped (a
+// skipped load reads zero).  In the normal build the test is constant true.
+struct Ctl;
+#ifdef CSAR_CHECKED
+__device__ __forceinline__ bool csar_in_range(size_t i, size_t n, Ctl* ctl);
+#define CSAR_CHECK(i, n, ctl) ::csar::csar_in_range((size_t)(i), (size_t)(n), (ctl))
+#else
+#define CSAR_CHECK(i, n, ctl) true
+#endif
 
 // Column-pass modes.
 enum ColMode : int {
@@ -72,6 +84,14 @@ struct Ctl {
   uint32_t sel_fused;    // 1: this iteration's selection runs in the one-CTA kernel
   uint32_t pad2;
 };
+
+#ifdef CSAR_CHECKED
+__device__ __forceinline__ bool csar_in_range(size_t i, size_t n, Ctl* ctl) {
+  if (i < n) return true;
+  if (ctl) atomicOr(&ctl->err, kErrIndex);
+  return false;
+}
+#endif
 
 // One-CTA selection (k_sel_fused): used when the union of support and candidates fits
 // in its shared memory and the step is fixed.

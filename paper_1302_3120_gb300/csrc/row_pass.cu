@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   float2* rp = a.data + (size_t)(live ? row : 0) * N;
   const float2* sp = a.src ? a.src + (size_t)(live ? row : 0) * N : rp;
   float2 v[R];
+  const bool ok_row = !live || CSAR_CHECK((size_t)row * N + (N - 1), (size_t)a.n_rows * N, a.ctl);
 #pragma unroll
-  for (int s = 0; s < R; ++s) v[s] = live ? __ldcs(&sp[t + s * QR]) : make_float2(0.f, 0.f);
+  for (int s = 0; s < R; ++s) v[s] = live && ok_row ? __ldcs(&sp[t + s * QR]) : make_float2(0.f, 0.f);
   if constexpr (kRowChains<N>) {
     // Gamma tables of this CTA's rows for the three phases: gam[(row*3 + phase)*R + u]
     for (int i = tid; i < WR * 3 * R; i += row_threads(N)) {
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
     const PhaseCoef c = cp->epi;
     phase_ap<R, 0, R>(v, c, t - N / 2, QR, a.scale, phase_second_diff(c, QR));
   }
-  if (live) {
+  if (live && ok_row) {
 #pragma unroll
     for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
   }

@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw
     if (!kept(key_of(b), s2)) continue;
     const uint32_t tile = (idx % (uint32_t)a.nr) / (uint32_t)a.col_tile;
     const uint32_t pos = atomicAdd(&a.tile_cur[tile], 1u);
+    if (!CSAR_CHECK(pos, a.n, c) || !CSAR_CHECK(idx, a.n, c)) continue;
     a.xo_idx[pos] = idx;
     a.xo_val[pos] = raw ? b : shrink(b, sigma, a.thresh);
   }
@@ -476,6 +477,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
       if (ix[u] == jstar) c->b_jstar = bv[u];
       if (!kept(key[e], s2)) continue;
       const uint32_t pos = atomicAdd(&tcnt[(ix[u] % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+      if (!CSAR_CHECK(pos, a.n, c) || !CSAR_CHECK(ix[u], a.n, c)) continue;
       a.xo_idx[pos] = ix[u];
       a.xo_val[pos] = shrink(bv[u], sigma, a.thresh);
     }

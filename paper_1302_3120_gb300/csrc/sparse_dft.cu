@@ -43,9 +43,13 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_ti
   if (tid < ne) {
     const uint32_t idx = a.xs_idx[e0 + tid];
     const uint32_t row = idx / (uint32_t)a.nr;
-    const uint32_t cl = idx % (uint32_t)a.nr - (uint32_t)col0;
-    key = (cl << 16) | row;                     // row < 2^13, column < 16
+    uint32_t cl = idx % (uint32_t)a.nr - (uint32_t)col0;
     val = a.xs_val[e0 + tid];
+    if (!CSAR_CHECK(cl, kDirectCols, a.ctl) || !CSAR_CHECK(row, N, a.ctl)) {
+      cl = 0u;
+      val = make_float2(0.f, 0.f);
+    }
+    key = (cl << 16) | row;                     // row < 2^13, column < 16
     e_key[tid] = key;
   }
   __syncthreads();
@@ -87,7 +91,8 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_ti
     // 256 rows x 16 columns: each half-warp writes one 128-byte row segment
     for (int i = tid; i < kSdRows * kDirectCols; i += kSdThreads) {
       const int r = i / kDirectCols, c = i % kDirectCols;
-      __stcs(&a.out[(size_t)(k0 + r) * a.nr + col0 + c], blk[r][c]);
+      const size_t gi = (size_t)(k0 + r) * a.nr + col0 + c;
+      if (CSAR_CHECK(gi, (size_t)N * a.nr, a.ctl)) __stcs(&a.out[gi], blk[r][c]);
     }
   }
 }
