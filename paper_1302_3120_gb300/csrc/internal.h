@@ -77,7 +77,7 @@ struct Ctl {
   float mu;              // step of the current iteration
   float sigma;           // threshold of the current iteration
   uint32_t jstar;        // flat index of the (K+1)-th largest |b| (0xffffffff: none)
-  uint32_t pad1;
+  float sigma_prev;      // threshold of the previous iteration (0: none yet)
   float2 b_jstar;        // b at jstar
   double niht_num;       // ||Delta X_Gamma||^2
   double niht_den;       // ||S . G(Delta X_Gamma)||^2

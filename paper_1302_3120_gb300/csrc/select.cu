@@ -32,6 +32,15 @@ constexpr int kGridThreads = 512;   // grid-stride kernels
 
 __device__ __forceinline__ uint32_t key_of(float2 b) { return __float_as_uint(cabs2(b)) & 0x7fffffffu; }
 
+// h[bin] += 1 for every lane of the (fully active) warp with bin >= 0, one atomic per
+// distinct bin: near the threshold the keys crowd into a few bins, where per-lane atomics
+// would serialise.
+__device__ __forceinline__ void hist_add_warp(uint32_t* h, int bin) {
+  if (!__any_sync(0xffffffffu, bin >= 0)) return;
+  const unsigned m = __match_any_sync(0xffffffffu, bin);
+  if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&h[bin], (uint32_t)__popc(m));
+}
+
 // b of union element e: on-support entries first (X + mu dX), then candidates (mu dX).
 __device__ __forceinline__ float2 union_b(const SelArgs& a, uint32_t e, uint32_t nx, float mu,
                                           uint32_t* idx) {
@@ -145,18 +154,55 @@ __device__ void check_capacity(const SelArgs& a, int lb) {
   if (cnt > a.cand_cap) atomicOr(&a.ctl->err, kErrCapacity);
 }
 
+// Fixed step: does the union of the support and the candidates (off-support |Delta X|^2
+// >= cut) already hold the K+1 largest |b|?  Every element left out has |b|^2 < mu^2 cut
+// (up to a few ulp), so it does when at least K+1 union elements have |b|^2 >= T =
+// mu^2 cut (1 + 2^-16): the support counted exactly, the candidates from the histogram
+// bins above that of cut (1 + 2^-14) (a lower bound).  Then the selection on the union is
+// exact whatever the (K+1)-th off-support key, and the candidate cut can sit just under
+// the expected threshold instead of under the (K+1)-th off-support magnitude.
+__device__ bool union_suffices(const SelArgs& a, unsigned long long* sh) {
+  const Ctl* c = a.ctl;
+  const uint32_t cut = c->cut_key;
+  if (a.mu_mode != 0 || cut == kNoCandidates || c->cand_count > a.cand_cap) return false;
+  const float mu = a.mu_fixed;
+  const uint32_t t_key = __float_as_uint(mu * mu * __uint_as_float(cut) * (1.f + 1.f / 65536.f));
+  const uint32_t cut_hi = __float_as_uint(__uint_as_float(cut) * (1.f + 1.f / 16384.f));
+  const int tid = threadIdx.x;
+  unsigned long long cnt = 0;
+  const uint32_t nx = c->nx;
+  for (uint32_t e = tid; e < nx; e += kSelThreads) {
+    uint32_t idx;
+    if (key_of(union_b(a, e, nx, mu, &idx)) >= t_key) ++cnt;
+  }
+  for (int i = (int)(cut_hi >> kHistShift) + 1 + tid; i < (int)kHistBins; i += kSelThreads) cnt += a.hist[i];
+  __syncthreads();
+  sh[tid] = cnt;
+  __syncthreads();
+  for (int off = kSelThreads / 2; off > 0; off >>= 1) {
+    if (tid < off) sh[tid] += sh[tid + off];
+    __syncthreads();
+  }
+  const bool ok = sh[0] >= (unsigned long long)a.K + 1;
+  __syncthreads();
+  return ok;
+}
+
 __global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
   __shared__ unsigned long long sh[kSelThreads];
   __shared__ uint32_t state;
   Ctl* c = a.ctl;
   const uint64_t target = (uint64_t)a.K + 1;
+  const bool suffices = union_suffices(a, sh);
   uint64_t above = 0;
   const int b = find_bin(a.hist, kHistBins, target, &above, sh);
   if (threadIdx.x == 0) {
     // the selection pass counted only keys >= hist_floor(cut): if fewer than K+1 lie
     // there, the (K+1)-th off-support key is below the floor and its bin is unknown
     const bool truncated = hist_floor(c->cut_key) > 0u;
-    if (b < 0 && truncated) {
+    if (suffices) {
+      c->need_repass = kRepassNone;
+    } else if (b < 0 && truncated) {
       c->need_repass = kRepassHist;
       c->cut_key = kNoCandidates;
       c->cand_count = 0u;
@@ -221,17 +267,18 @@ __global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level
   const uint32_t nu = union_size(c, a.cand_cap);
   const float mu = c->mu;
   const uint32_t prefix = c->sel_prefix;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < nu; e0 += stride) {   // uniform per block
+    const uint32_t e = e0 + threadIdx.x;
     uint32_t idx;
-    const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
-    if (key < kMinKey) continue;
-    if (level == 0) {
-      atomicAdd(&h[key >> 20], 1u);
-    } else if (level == 1) {
-      if ((key >> 20) == prefix) atomicAdd(&h[(key >> 8) & 4095u], 1u);
-    } else {
-      if ((key >> 8) == prefix) atomicAdd(&h[key & 255u], 1u);
+    const uint32_t key = e < nu ? key_of(union_b(a, e, nx, mu, &idx)) : 0u;
+    int bin = -1;
+    if (key >= kMinKey) {
+      if (level == 0) bin = (int)(key >> 20);
+      else if (level == 1) bin = (key >> 20) == prefix ? (int)((key >> 8) & 4095u) : -1;
+      else bin = (key >> 8) == prefix ? (int)(key & 255u) : -1;
     }
+    hist_add_warp(h, bin);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x)
@@ -387,12 +434,16 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
     const int nb = level == 2 ? 256 : (int)kHistBins;
     for (int i = tid; i < nb; i += kSelThreads) h[i] = 0u;
     __syncthreads();
-    for (uint32_t e = tid; e < nu; e += kSelThreads) {
-      const uint32_t k = key[e];
-      if (k < kMinKey) continue;
-      if (level == 0) atomicAdd(&h[k >> 20], 1u);
-      else if (level == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 4095u], 1u); }
-      else if ((k >> 8) == prefix) atomicAdd(&h[k & 255u], 1u);
+    for (uint32_t e0 = 0; e0 < nu; e0 += kSelThreads) {   // uniform trip count (warp votes)
+      const uint32_t e = e0 + tid;
+      const uint32_t k = e < nu ? key[e] : 0u;
+      int bin = -1;
+      if (k >= kMinKey) {
+        if (level == 0) bin = (int)(k >> 20);
+        else if (level == 1) bin = (k >> 20) == prefix ? (int)((k >> 8) & 4095u) : -1;
+        else bin = (k >> 8) == prefix ? (int)(k & 255u) : -1;
+      }
+      hist_add_warp(h, bin);
     }
     __syncthreads();
     uint64_t above = 0;
@@ -554,11 +605,20 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
     st.pad = 0;
     if (a.stats) a.stats[c->iter] = st;
     c->iter += 1u;
-    // next cut on |Delta X|^2: half of (sigma/mu)^2, i.e. 3 dB below the current
-    // threshold (checked, and re-done exactly if wrong, by the next sel_check)
+    // next cut on |Delta X|^2 (checked, and re-done exactly if wrong, by the next
+    // sel_check): with a fixed step, (rho sigma / mu)^2 with rho = 0.95 times the last
+    // ratio sigma_i / sigma_(i-1) when that falls below 1 (the threshold of the next
+    // iteration is expected near sigma r), 0.7 before a ratio is known; with the NIHT
+    // step (mu changes between iterations) half of (sigma/mu)^2
     const float mu = c->mu > 0.f ? c->mu : 1.f;
     const float s = c->sigma / mu;
-    float g = 0.5f * s * s;
+    float rho2 = 0.5f;
+    if (a.mu_mode == 0 && c->sigma_prev > 0.f) {
+      const float r = fminf(1.f, c->sigma / c->sigma_prev);
+      rho2 = (0.95f * r) * (0.95f * r);
+    }
+    c->sigma_prev = c->sigma;
+    float g = rho2 * s * s;
     uint32_t cut = __float_as_uint(g);
     if (!(g > 0.f) || !isfinite(g)) cut = kNoCandidates;
     if (cut < kMinKey) cut = kMinKey;
