@@ -417,18 +417,9 @@ __global__ void __launch_bounds__(ColCfg<N, P, E>::NT, col_ctas_per_sm(E)) k_col
       const float2 d = cscale(v[s], a.scale);
       const bool on_support = (sup >> s) & 1u;
       const uint32_t key = __float_as_uint(cabs2(d)) & 0x7fffffffu;
-      if (hist_on) {
-        // one shared-memory atomic per distinct bin of the warp (keys near the cut crowd
-        // into a few bins)
-        int hb = -1;
-        if (!on_support && key >= floor_key) {
-          hb = (int)(key >> kHistShift) - hb0;
-          hb = hb < nbins ? hb : nbins - 1;
-        }
-        if (__any_sync(full, hb >= 0)) {
-          const unsigned mm = __match_any_sync(full, hb);
-          if (hb >= 0 && lane == __ffs(mm) - 1) atomicAdd(&hist[hb], (uint32_t)__popc(mm));
-        }
+      if (hist_on && !on_support && key >= floor_key) {
+        const int hb = (int)(key >> kHistShift) - hb0;
+        atomicAdd(&hist[hb < nbins ? hb : nbins - 1], 1u);
       }
       const bool take = !on_support && key >= cut && key >= kMinKey;
       const uint32_t bal = __ballot_sync(full, take);

@@ -32,15 +32,6 @@ constexpr int kGridThreads = 512;   // grid-stride kernels
 
 __device__ __forceinline__ uint32_t key_of(float2 b) { return __float_as_uint(cabs2(b)) & 0x7fffffffu; }
 
-// h[bin] += 1 for every lane of the (fully active) warp with bin >= 0, one atomic per
-// distinct bin: near the threshold the keys crowd into a few bins, where per-lane atomics
-// would serialise.
-__device__ __forceinline__ void hist_add_warp(uint32_t* h, int bin) {
-  if (!__any_sync(0xffffffffu, bin >= 0)) return;
-  const unsigned m = __match_any_sync(0xffffffffu, bin);
-  if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&h[bin], (uint32_t)__popc(m));
-}
-
 // b of union element e: on-support entries first (X + mu dX), then candidates (mu dX).
 __device__ __forceinline__ float2 union_b(const SelArgs& a, uint32_t e, uint32_t nx, float mu,
                                           uint32_t* idx) {
@@ -267,18 +258,17 @@ __global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level
   const uint32_t nu = union_size(c, a.cand_cap);
   const float mu = c->mu;
   const uint32_t prefix = c->sel_prefix;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < nu; e0 += stride) {   // uniform per block
-    const uint32_t e = e0 + threadIdx.x;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
     uint32_t idx;
-    const uint32_t key = e < nu ? key_of(union_b(a, e, nx, mu, &idx)) : 0u;
-    int bin = -1;
-    if (key >= kMinKey) {
-      if (level == 0) bin = (int)(key >> 20);
-      else if (level == 1) bin = (key >> 20) == prefix ? (int)((key >> 8) & 4095u) : -1;
-      else bin = (key >> 8) == prefix ? (int)(key & 255u) : -1;
+    const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
+    if (key < kMinKey) continue;
+    if (level == 0) {
+      atomicAdd(&h[key >> 20], 1u);
+    } else if (level == 1) {
+      if ((key >> 20) == prefix) atomicAdd(&h[(key >> 8) & 4095u], 1u);
+    } else {
+      if ((key >> 8) == prefix) atomicAdd(&h[key & 255u], 1u);
     }
-    hist_add_warp(h, bin);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x)
@@ -434,16 +424,12 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
     const int nb = level == 2 ? 256 : (int)kHistBins;
     for (int i = tid; i < nb; i += kSelThreads) h[i] = 0u;
     __syncthreads();
-    for (uint32_t e0 = 0; e0 < nu; e0 += kSelThreads) {   // uniform trip count (warp votes)
-      const uint32_t e = e0 + tid;
-      const uint32_t k = e < nu ? key[e] : 0u;
-      int bin = -1;
-      if (k >= kMinKey) {
-        if (level == 0) bin = (int)(k >> 20);
-        else if (level == 1) bin = (k >> 20) == prefix ? (int)((k >> 8) & 4095u) : -1;
-        else bin = (k >> 8) == prefix ? (int)(k & 255u) : -1;
-      }
-      hist_add_warp(h, bin);
+    for (uint32_t e = tid; e < nu; e += kSelThreads) {
+      const uint32_t k = key[e];
+      if (k < kMinKey) continue;
+      if (level == 0) atomicAdd(&h[k >> 20], 1u);
+      else if (level == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 4095u], 1u); }
+      else if ((k >> 8) == prefix) atomicAdd(&h[k & 255u], 1u);
     }
     __syncthreads();
     uint64_t above = 0;
