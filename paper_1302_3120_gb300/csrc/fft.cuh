@@ -34,8 +34,32 @@ __host__ __device__ constexpr int regs_for(int q) { return q >= 32 ? 32 : 16; }
 // values per thread in the column passes (more warps per SM to hide shared-memory latency)
 __host__ __device__ constexpr int col_regs(int q) { return 16; }
 
+// Complex add and subtract as one packed two-lane FP32 instruction each (sm_100-class
+// f32x2 arithmetic; every lane rounds to nearest like the scalar instruction, so the
+// results are the same).  -DCSAR_SCALAR_COMPLEX restores the scalar pairs.
+#ifdef CSAR_SCALAR_COMPLEX
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#else
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  float2 o;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(o.x), "=f"(o.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return o;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 o;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(o.x), "=f"(o.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return o;
+}
+#endif
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
