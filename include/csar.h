@@ -295,10 +295,11 @@ csar_status csar_solve_batched(csar_batch batch, const void* const* Y_dev,
 csar_status csar_batch_check(csar_batch batch);
 
 /* Autotuner: times `iters` ITA iterations on synthetic data for every column-pass
- * configuration available for (n_az, n_rg), keeps the fastest for plans created
- * afterwards in this process (and in the file named by CSAR_TUNE_FILE, if set), and
- * returns it in *chosen_cluster.  Every CTA size (half, full and wide tiles) is
- * tried; *chosen_cluster reports the cluster size of the chosen configuration.
+ * configuration available for (n_az, n_rg) and, for rows of 1024 bins and more, both
+ * radix schedules of the range passes (32 values per thread: 8192 = 8 x 32 x 32; 16:
+ * 2 x 16 x 16 x 16), keeps the fastest for plans created afterwards in this process (and
+ * in the file named by CSAR_TUNE_FILE, if set), and returns the column configuration's
+ * cluster size in *chosen_cluster.  Every CTA size (half, full and wide tiles) is tried.
  * Synchronises the device; allocates temporaries. */
 csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* chosen_cluster);
 

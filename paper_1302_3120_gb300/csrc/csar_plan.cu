@@ -264,6 +264,7 @@ csar_status set_error(csar_status st, const char* msg) { return fail(st, "%s", m
 namespace {
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, std::pair<ColConf, ColConf>> g_tune;   // (main, residue)
+std::map<std::pair<int, int>, int> g_tune_row;   // values per thread of the range passes
 bool g_tune_loaded = false;
 
 void tune_load_locked() {
@@ -273,8 +274,13 @@ void tune_load_locked() {
   if (!f) return;
   FILE* fp = std::fopen(f, "r");
   if (!fp) return;
-  int na, nr, p, e, pr, er;
-  while (std::fscanf(fp, "%d %d %d %d %d %d", &na, &nr, &p, &e, &pr, &er) == 6) {
+  // one line per (n_az, n_rg): main and residue column configurations, then (optional)
+  // the range passes' values per thread
+  char line[256];
+  while (std::fgets(line, sizeof line, fp)) {
+    int na, nr, p, e, pr, er, rr = 0;
+    const int got = std::sscanf(line, "%d %d %d %d %d %d %d", &na, &nr, &p, &e, &pr, &er, &rr);
+    if (got < 6) continue;
     ColConf c, r;
     c.p = p;
     c.e = e;
@@ -282,6 +288,7 @@ void tune_load_locked() {
     r.e = er;
     if (col_conf_ok(na, c) && col_conf_ok(na, r) && col_w(na, p, e) == col_w(na, pr, er))
       g_tune[{na, nr}] = {c, r};
+    if (got == 7 && (rr == 16 || rr == 32)) g_tune_row[{na, nr}] = rr;
   }
   std::fclose(fp);
 }
@@ -291,9 +298,12 @@ void tune_save_locked() {
   if (!f) return;
   FILE* fp = std::fopen(f, "w");
   if (!fp) return;
-  for (const auto& kv : g_tune)
-    std::fprintf(fp, "%d %d %d %d %d %d\n", kv.first.first, kv.first.second, kv.second.first.p,
-                 kv.second.first.e, kv.second.second.p, kv.second.second.e);
+  for (const auto& kv : g_tune) {
+    const auto rr = g_tune_row.find(kv.first);
+    std::fprintf(fp, "%d %d %d %d %d %d %d\n", kv.first.first, kv.first.second, kv.second.first.p,
+                 kv.second.first.e, kv.second.second.p, kv.second.second.e,
+                 rr == g_tune_row.end() ? 32 : rr->second);
+  }
   std::fclose(fp);
 }
 
@@ -306,6 +316,14 @@ bool tuned_conf(int na, int nr, ColConf* c, ColConf* r) {
   *r = it->second.second;
   return true;
 }
+
+// Values per thread of the range passes chosen by the autotuner (0: none, the default).
+int tuned_row_regs(int na, int nr) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune_row.find({na, nr});
+  return it == g_tune_row.end() || it->second == 32 ? 0 : it->second;
+}
 }  // namespace
 
 struct csar_plan_s {
@@ -316,6 +334,7 @@ struct csar_plan_s {
   ColConf col;                    // column-pass configuration (cluster size, values per CTA)
   ColConf col_res;                // configuration of the residue and NIHT-norm passes (same W)
   int sel_fused_ok = 1;           // one-CTA selection allowed (CSAR_SEL_FUSED=0 disables it)
+  int row_regs = 0;               // values per thread of the range passes (0: default 32; 16)
   int col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
@@ -458,6 +477,7 @@ RowArgs row_args(csar_plan plan, float2* data, const RowCoef* coef) {
   r.tw = plan->tw;
   r.n_rows = plan->na;
   r.scale = 1.0f / (float)plan->nr;
+  r.regs = plan->row_regs;
   return r;
 }
 
@@ -1003,6 +1023,8 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   plan->col_tile = col_w(plan->na, plan->col.p, plan->col.e);
   plan->n_tiles = plan->nr / plan->col_tile;
   if (const char* sf = std::getenv("CSAR_SEL_FUSED")) plan->sel_fused_ok = sf[0] != '0';
+  plan->row_regs = tuned_row_regs(plan->na, plan->nr);
+  if (const char* rr = std::getenv("CSAR_ROW_REGS")) plan->row_regs = std::atoi(rr) == 16 ? 16 : 0;
   const char* ng = std::getenv("CSAR_NO_GRAPH");
   plan->use_graphs = !(ng && ng[0] == '1');
   auto bail = [&](csar_status st) {
@@ -1566,6 +1588,25 @@ csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* cho
       if (ok) trials.push_back({c, col_w(na, c.p, c.e), pass[0] + pass[4] + pass[5], pass[2]});
     }
   }
+  // radix schedule of the range passes (values per thread, 32 or 16 for rows of 1024
+  // bins and more): the summed time of the two range passes decides
+  int best_regs = 32;
+  if (nr >= 1024) {
+    float best_row = -1.f;
+    for (int regs : {32, 16}) {
+      csar_plan plan = nullptr;
+      if (csar_plan_create(params, 0u, &plan) != CSAR_OK) continue;
+      plan->row_regs = regs == 16 ? 16 : 0;
+      float pass[kPasses] = {};
+      const bool ok = csar_solve(plan, y, m, x, &o, nullptr, nullptr) == CSAR_OK &&
+                      csar_solve_profile(plan, y, m, x, &o, pass, kPasses, nullptr) == CSAR_OK;
+      csar_plan_destroy(plan);
+      if (ok && (best_row < 0.f || pass[1] + pass[3] < best_row)) {
+        best_row = pass[1] + pass[3];
+        best_regs = regs;
+      }
+    }
+  }
   cudaFree(y);
   cudaFree(x);
   cudaFree(m);
@@ -1587,6 +1628,7 @@ csar_status csar_autotune(const csar_params* params, int32_t iters, int32_t* cho
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load_locked();
     g_tune[{na, nr}] = {best, best_res};
+    g_tune_row[{na, nr}] = best_regs;
     tune_save_locked();
   }
   if (chosen_cluster) *chosen_cluster = best.p;

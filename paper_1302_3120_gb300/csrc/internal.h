@@ -156,6 +156,7 @@ struct RowArgs {
   float* partial;
   Ctl* ctl;
   float resid_scale;
+  int regs;                 // values per thread of the range transforms: 32 (default) or 16
 };
 
 // Range-Doppler operator pair (rda_pass.cu): per azimuth-frequency row, the migration

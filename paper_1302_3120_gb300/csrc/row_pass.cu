@@ -34,13 +34,18 @@ constexpr bool kRowChains = N >= 1024;
 template <int N>
 constexpr bool kBulkY = N == 8192;
 
+// Threads of a CTA with R values per thread.
+__host__ __device__ constexpr int row_threads_r(int n, int r) { return n * row_w(n) / r; }
+
 // RESID: the residue form (a.yf set), a separate instance so that the plain pass
-// carries none of its code.
-template <int N, bool RESID>
-__global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
+// carries none of its code.  R: values per thread, which sets the radix schedule of the
+// transforms (R = 32: 8192 = 8 x 32 x 32, two exchanges; R = 16: 2 x 16 x 16 x 16, three
+// exchanges and twice the threads per row); the plan chooses (autotuner, CSAR_ROW_REGS).
+template <int N, bool RESID, int R = regs_for(N)>
+__global__ void __launch_bounds__(row_threads_r(N, R), 2) k_row(RowArgs a) {
   constexpr int WR = row_w(N);
-  constexpr int R = regs_for(N);
   constexpr int QR = N / R;
+  constexpr int NTR = row_threads_r(N, R);
   using L = Layout<N, WR, false>;
   extern __shared__ float2 smem[];
   if (a.gate && *a.gate != a.gate_val) return;
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   for (int s = 0; s < R; ++s) v[s] = live && ok_row ? __ldcs(&sp[t + s * QR]) : make_float2(0.f, 0.f);
   if constexpr (kRowChains<N>) {
     // Gamma tables of this CTA's rows for the three phases: gam[(row*3 + phase)*R + u]
-    for (int i = tid; i < WR * 3 * R; i += row_threads(N)) {
+    for (int i = tid; i < WR * 3 * R; i += NTR) {
       const int rw = blockIdx.x * WR + i / (3 * R);
       const RowCoef& rc = a.coef[rw < a.n_rows ? rw : 0];
       const int ph = (i / R) % 3;
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);
-    constexpr int kWarps = row_threads(N) / 32;
+    constexpr int kWarps = NTR / 32;
     if ((tid & 31) == 0) red[tid >> 5] = acc;
     __syncthreads();
     if (tid == 0) {
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   // in a rolled loop: half the instruction footprint of two unrolled transforms.
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
-    fft<N, false, L, false>(v, sm, tw, t, w);
+    fft<N, false, L, false, R>(v, sm, tw, t, w);
     if (pass == 1) break;
     // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
     if constexpr (kRowChains<N>) {
@@ -173,27 +178,46 @@ __global__ void __launch_bounds__(row_threads(N), 2) k_row(RowArgs a) {
   }
 }
 
-template <int N>
+template <int N, int R = regs_for(N)>
 static size_t row_smem() {
   using L = Layout<N, row_w(N), false>;
   return (size_t)L::kSmemElems * sizeof(float2) + (kTwLo + kTwHi) * sizeof(float2) +
          32 * sizeof(float) + 2 * sizeof(float2) +
-         (kRowChains<N> ? (size_t)row_w(N) * 3 * regs_for(N) * sizeof(float2) : 0);
+         (kRowChains<N> ? (size_t)row_w(N) * 3 * R * sizeof(float2) : 0);
+}
+
+// The radix-16 schedule (16 values per thread) is built for rows of 1024 bins and more.
+template <int N>
+constexpr bool kRow16 = N >= 1024;
+
+template <int N, int R>
+static cudaError_t row_attrs_r() {
+  cudaError_t e = cudaFuncSetAttribute(k_row<N, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)row_smem<N, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_row<N, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)row_smem<N, R>());
+  return e;
+}
+
+template <int N, int R>
+static cudaError_t row_launch_r(const RowArgs& a, cudaStream_t s) {
+  const int grid = (a.n_rows + row_w(N) - 1) / row_w(N);
+  if (a.yf) k_row<N, true, R><<<grid, row_threads_r(N, R), row_smem<N, R>(), s>>>(a);
+  else k_row<N, false, R><<<grid, row_threads_r(N, R), row_smem<N, R>(), s>>>(a);
+  return cudaGetLastError();
 }
 
 #define CSAR_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
 cudaError_t row_set_attributes(int nr) {
   switch (nr) {
-#define CSAR_CASE(N)                                                                         \
-  case N: {                                                                                  \
-    cudaError_t e = cudaFuncSetAttribute(k_row<N, false>,                                    \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                         (int)row_smem<N>());                                \
-    if (e == cudaSuccess)                                                                    \
-      e = cudaFuncSetAttribute(k_row<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                               (int)row_smem<N>());                                          \
-    return e;                                                                                \
+#define CSAR_CASE(N)                                                   \
+  case N: {                                                            \
+    cudaError_t e = row_attrs_r<N, regs_for(N)>();                     \
+    if constexpr (kRow16<N>)                                           \
+      if (e == cudaSuccess) e = row_attrs_r<N, (kRow16<N> ? 16 : regs_for(N))>(); \
+    return e;                                                          \
   }
     CSAR_ROW_SIZES(CSAR_CASE)
 #undef CSAR_CASE
@@ -203,13 +227,11 @@ cudaError_t row_set_attributes(int nr) {
 
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s) {
   switch (nr) {
-#define CSAR_CASE(N)                                                              \
-  case N: {                                                                       \
-    const int grid = (a.n_rows + row_w(N) - 1) / row_w(N);                        \
-    if (a.yf) k_row<N, true><<<grid, row_threads(N), row_smem<N>(), s>>>(a);      \
-    else k_row<N, false><<<grid, row_threads(N), row_smem<N>(), s>>>(a);          \
-    return cudaGetLastError();                                                    \
-  }
+#define CSAR_CASE(N)                                                                       \
+  case N:                                                                                  \
+    if constexpr (kRow16<N>)                                                               \
+      if (a.regs == 16) return row_launch_r<N, (kRow16<N> ? 16 : regs_for(N))>(a, s);     \
+    return row_launch_r<N, regs_for(N)>(a, s);
     CSAR_ROW_SIZES(CSAR_CASE)
 #undef CSAR_CASE
     default: return cudaErrorInvalidValue;
