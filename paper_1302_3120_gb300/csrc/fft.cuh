@@ -107,6 +107,37 @@ __device__ __forceinline__ float2 twiddle_const(float2 a, int k) {
   return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
 }
 
+// Radix-2 butterfly with a constant twiddle: lo = e + o W, hi = e - o W, W = W_RS^k
+// (conjugate for the inverse).  Trivial twiddles (1, -i, -1, +i) keep the plain product;
+// for the others W = c + i s is split as m (r + i) or m (1 + i r) with m the larger of
+// |c|, |s| and |r| <= 1 (the tangent form of the butterfly): u = o (W / m) takes two
+// FMAs and lo, hi = e +- m u four more, 6 FP32 operations per butterfly instead of 8.
+template <int RS, bool INV>
+__device__ __forceinline__ void bfly_const(float2 e, float2 o, int k, float2& lo, float2& hi) {
+  const int j = (k * (32 / RS)) & 31;   // angle 2 pi j / 32
+  if (j % 8 == 0) {
+    const float2 t = twiddle_const<RS, INV>(o, k);
+    lo = cadd(e, t);
+    hi = csub(e, t);
+    return;
+  }
+  const float c = cos32(j);
+  const float s = INV ? cos32(j - 8) : -cos32(j - 8);   // sin(2 pi j/32) = cos(2 pi (j-8)/32)
+  float2 u;
+  float m;
+  if (fabsf(c) >= fabsf(s)) {   // W = c (1 + i r), r = s / c
+    const float r = s / c;
+    u = make_float2(fmaf(-o.y, r, o.x), fmaf(o.x, r, o.y));
+    m = c;
+  } else {                      // W = s (r + i), r = c / s
+    const float r = c / s;
+    u = make_float2(fmaf(o.x, r, -o.y), fmaf(o.y, r, o.x));
+    m = s;
+  }
+  lo = make_float2(fmaf(m, u.x, e.x), fmaf(m, u.y, e.y));
+  hi = make_float2(fmaf(-m, u.x, e.x), fmaf(-m, u.y, e.y));
+}
+
 // In-place length-RS DFT on a[0..RS-1], natural order in and out (radix-2 DIT).
 template <int RS, bool INV>
 struct Dft {
@@ -118,9 +149,7 @@ struct Dft {
     Dft<RS / 2, INV>::run(o);
 #pragma unroll
     for (int k = 0; k < RS / 2; ++k) {
-      const float2 t = twiddle_const<RS, INV>(o[k], k);
-      a[k] = cadd(e[k], t);
-      a[k + RS / 2] = csub(e[k], t);
+      bfly_const<RS, INV>(e[k], o[k], k, a[k], a[k + RS / 2]);
     }
   }
 };

@@ -102,8 +102,10 @@ __device__ __forceinline__ float2 phase_gamma(const PhaseCoef& c, int d, int u) 
 // so the factor is E Lambda^u Gamma[u] with E = exp(j 2 pi phi(i0)), Lambda =
 // exp(j 2 pi kappa) = exp(j 2 pi (phi(i0 + d) - phi(i0))) conj(Gamma[1]) and Gamma the
 // per-row table of phase_gamma.  Two exact evaluations per chain and three complex
-// products per element; the powers Lambda^u accumulate one rounding per step (a few
-// 1e-7 over 32 steps), the quadratic part comes exact from the table.
+// products per element; the quadratic part comes exact from the table.  The powers
+// Lambda^u run as four interleaved recurrences (u = 4m + j: E Lambda^j times
+// (Lambda^4)^m), which gives the scheduler four independent dependency chains instead
+// of one and accumulates at most S1/4 + 3 roundings per power (a few 1e-7).
 template <int R, int S0, int S1>
 __device__ __forceinline__ void phase_chain(float2 (&v)[R], const PhaseCoef& c, int i0, int d,
                                             float scale, const float2* gam) {
@@ -112,14 +114,19 @@ __device__ __forceinline__ void phase_chain(float2 (&v)[R], const PhaseCoef& c, 
   const float2 q = make_float2(fmaf(e1.x, e0.x, e1.y * e0.y), fmaf(e1.y, e0.x, -e1.x * e0.y));  // e1 conj(e0)
   const float2 g1 = gam[1];
   const float2 lam = make_float2(fmaf(q.x, g1.x, q.y * g1.y), fmaf(q.y, g1.x, -q.x * g1.y));  // q conj(g1)
-  float2 p = make_float2(e0.x * scale, e0.y * scale);
-  v[S0] = cmul(v[S0], p);
+  const float2 p0 = make_float2(e0.x * scale, e0.y * scale);
 #pragma unroll
   for (int s = S0 + 1; s < S1; ++s) v[s] = cmul(v[s], gam[s - S0]);
+  const float2 lam2 = cmul(lam, lam), lam4 = cmul(lam2, lam2);
+  float2 p[4];
+  p[0] = p0;
+  p[1] = cmul(p0, lam);
+  p[2] = cmul(p0, lam2);
+  p[3] = cmul(p[1], lam2);
 #pragma unroll
-  for (int s = S0 + 1; s < S1; ++s) {
-    p = cmul(p, lam);
-    v[s] = cmul(v[s], p);
+  for (int s = S0; s < S1; ++s) {
+    v[s] = cmul(v[s], p[(s - S0) & 3]);
+    p[(s - S0) & 3] = cmul(p[(s - S0) & 3], lam4);
   }
 }
 
