@@ -121,8 +121,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Tensor map of an [na][nr] complex64 array (8-byte elements) with boxes of
-// box_cols x box_rows; the base must be 16-byte aligned.
-static cudaError_t encode_map(CUtensorMap* map, const void* base, int na, int nr, int box_cols, int box_rows) {
+// box_cols x box_rows; the base must be 16-byte aligned.  swizzle128: the box's rows of
+// 128 bytes are stored in shared memory with their 16-byte chunks XOR-permuted by the
+// row index mod 8 (box_cols must then be 16).
+cudaError_t encode_map(CUtensorMap* map, const void* base, int na, int nr, int box_cols, int box_rows,
+                       bool swizzle128) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn || ((uintptr_t)base & 15u)) return cudaErrorInvalidValue;
   const cuuint64_t dim[2] = {(cuuint64_t)nr, (cuuint64_t)na};
@@ -138,7 +141,8 @@ static cudaError_t encode_map(CUtensorMap* map, const void* base, int na, int nr
                                     : promo >= 64  ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
                                                    : CU_TENSOR_MAP_L2_PROMOTION_NONE;
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dim, stride, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, l2,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -155,7 +159,7 @@ static cudaError_t launch_colp(int na, ColConf c, ColMode mode, const ColArgs& a
     default: return cudaErrorInvalidValue;
   }
   CUtensorMap map;
-  if (cudaError_t e = encode_map(&map, a.in, na, a.nr, bc, br)) return e;
+  if (cudaError_t e = encode_map(&map, a.in, na, a.nr, bc, br, false)) return e;
   switch (conf_key(na, c.p, c.e)) {
 #define CSAR_CASE(N, P, E) \
   case conf_key(N, P, E): return colp_launch_##N##_##P##_##E(mode, map, a, n_tiles, s);

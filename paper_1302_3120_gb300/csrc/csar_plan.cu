@@ -1041,6 +1041,7 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   PK(col_set_attributes(plan->na, plan->col));
   PK(col_set_attributes(plan->na, plan->col_res));
   PK(row_set_attributes(plan->nr));
+  PK(sparse_dft_set_attributes(plan->na));
   PK(dalloc(&plan->coef_g, plan->na));
   PK(dalloc(&plan->coef_m, plan->na));
   PK(cudaMemcpy(plan->coef_g, cg.data(), cg.size() * sizeof(RowCoef), cudaMemcpyHostToDevice));

@@ -231,6 +231,12 @@ ColConf col_conf_persist(int na);       // persistent passes: clusters of N_a/10
 cudaError_t launch_col(int na, ColConf conf, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);
+cudaError_t sparse_dft_set_attributes(int na);
+// Tensor map (cuTensorMapEncodeTiled) of an [na][nr] complex64 array with boxes of
+// box_cols x box_rows (col_dispatch.cu); the map is named by its struct tag so that this
+// header needs no driver API header.
+cudaError_t encode_map(struct CUtensorMap_st* map, const void* base, int na, int nr, int box_cols,
+                       int box_rows, bool swizzle128);
 cudaError_t launch_mask_apply(const float2* y, const uint32_t* mask_bits, float2* out, long long n,
                               cudaStream_t s);
 cudaError_t col_set_attributes(int na, ColConf conf);

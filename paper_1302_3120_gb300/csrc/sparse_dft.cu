@@ -6,24 +6,45 @@
 // the group's entries are bucketed by column in shared memory, one warp per column
 // accumulates its own entries for 8 output rows per lane (the twiddle advances by
 // W_N^(32 row_e) per row step from an exact table start), and a 256 x 16 block is
-// staged in shared memory and written as 128-byte row segments.
+// staged in shared memory and written to global memory by one tensor copy
+// (cp.async.bulk.tensor, 128-byte rows, 128-byte swizzle so that the column-wise
+// staging writes spread over the banks), double-buffered so that the copy of one chunk
+// overlaps the sums of the next: the pass issues no per-element store instructions.
 // Groups with more entries are left to the FFT path (k_col, COL_SPARSE_FWD).
+#include <cuda.h>
+
 #include "fft.cuh"
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace csar {
 
 constexpr int kSdThreads = 512;               // 16 warps = 16 columns
 constexpr int kSdRows = kDirectRows;          // output rows per chunk (8 per lane)
+constexpr int kSdBlkBytes = kSdRows * kDirectCols * (int)sizeof(float2);   // 32 KiB staging block
+// dynamic shared memory: two staging blocks (1024-byte aligned for the swizzle), then the
+// twiddles and the entry lists
+constexpr size_t kSdSmem = 1024 + 2 * kSdBlkBytes + (kTwLo + kTwHi) * sizeof(float2) +
+                           kDirectMaxEntries * (2 * sizeof(uint32_t) + sizeof(float2)) +
+                           (kDirectCols + 1) * sizeof(int);
+
+// Byte offset of element (r, c) of a staging block: rows of 128 bytes whose 16-byte
+// chunks are permuted by XOR with r mod 8 (the tensor map's 128-byte swizzle).
+__device__ __forceinline__ uint32_t blk_off(int r, int c) {
+  return (uint32_t)(r * 128 + (((c >> 1) ^ (r & 7)) << 4) + ((c & 1) << 3));
+}
 
 template <int N>
-__global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_tile, int chunks_per_cta) {
-  __shared__ float2 tw[kTwLo + kTwHi];
-  __shared__ uint32_t e_key[kDirectMaxEntries];   // flat index, then (column, row) order key
-  __shared__ uint32_t e_row[kDirectMaxEntries];
-  __shared__ float2 e_val[kDirectMaxEntries];
-  __shared__ int col_beg[kDirectCols + 1];
-  __shared__ float2 blk[kSdRows][kDirectCols + 1];
+__global__ void __launch_bounds__(kSdThreads) k_sparse_dft(const __grid_constant__ CUtensorMap omap, ColArgs a,
+                                                           int col_tile, int chunks_per_cta) {
+  extern __shared__ unsigned char sd_smem[];
+  const uint32_t sbase = (smem_addr(sd_smem) + 1023u) & ~1023u;
+  unsigned char* const blk = sd_smem + (sbase - smem_addr(sd_smem));
+  float2* tw = reinterpret_cast<float2*>(blk + 2 * kSdBlkBytes);
+  uint32_t* e_key = reinterpret_cast<uint32_t*>(tw + kTwLo + kTwHi);   // flat index, then (column, row) key
+  uint32_t* e_row = e_key + kDirectMaxEntries;
+  float2* e_val = reinterpret_cast<float2*>(e_row + kDirectMaxEntries);
+  int* col_beg = reinterpret_cast<int*>(e_val + kDirectMaxEntries);
   if (a.gate && *a.gate != a.gate_val) return;
   const int grp = blockIdx.x;
   const int bpg = kDirectCols / col_tile > 0 ? kDirectCols / col_tile : 1;
@@ -68,6 +89,7 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_ti
   const int w = tid >> 5, lane = tid & 31;
   const int i0 = col_beg[w], i1 = col_beg[w + 1];
   constexpr int kScale = kTwN / N;            // W_N^m = W_8192^(m * kScale)
+  const bool in_range = CSAR_CHECK((size_t)col0 + kDirectCols - 1, (size_t)a.nr, a.ctl);
   for (int ch = 0; ch < chunks_per_cta; ++ch) {
     const int k0 = (blockIdx.y * chunks_per_cta + ch) * kSdRows;
     float2 acc[8];
@@ -84,32 +106,57 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(ColArgs a, int col_ti
         e = cmul(e, st);
       }
     }
+    // staging block ch % 2 is free once the copy issued two chunks ago has read it
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
     __syncthreads();
+    unsigned char* const bk = blk + (ch & 1) * kSdBlkBytes;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) blk[lane + 32 * j][w] = acc[j];
+    for (int j = 0; j < 8; ++j) *reinterpret_cast<float2*>(bk + blk_off(lane + 32 * j, w)) = acc[j];
+    // the staging writes become visible to the tensor copy (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // 256 rows x 16 columns: each half-warp writes one 128-byte row segment
-    for (int i = tid; i < kSdRows * kDirectCols; i += kSdThreads) {
-      const int r = i / kDirectCols, c = i % kDirectCols;
-      const size_t gi = (size_t)(k0 + r) * a.nr + col0 + c;
-      if (CSAR_CHECK(gi, (size_t)N * a.nr, a.ctl)) __stcs(&a.out[gi], blk[r][c]);
+    if (tid == 0 && in_range && CSAR_CHECK((size_t)k0 + kSdRows - 1, (size_t)N, a.ctl)) {
+      asm volatile(
+          "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n\t"
+          "cp.async.bulk.commit_group;" ::"l"(&omap),
+          "r"(col0), "r"(k0), "r"(sbase + (uint32_t)((ch & 1) * kSdBlkBytes))
+          : "memory");
     }
+  }
+  // the copies complete (their writes performed) before the CTA's shared memory is released
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int N>
+static cudaError_t sd_attrs() {
+  return cudaFuncSetAttribute(k_sparse_dft<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdSmem);
+}
+
+cudaError_t sparse_dft_set_attributes(int na) {
+  switch (na) {
+    case 256: return sd_attrs<256>();
+    case 512: return sd_attrs<512>();
+    case 1024: return sd_attrs<1024>();
+    case 2048: return sd_attrs<2048>();
+    case 4096: return sd_attrs<4096>();
+    case 8192: return sd_attrs<8192>();
+    default: return cudaSuccess;
   }
 }
 
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s) {
   if (a.nr < kDirectCols || na < kSdRows) return cudaSuccess;   // small grids: FFT path only
+  CUtensorMap omap;
+  if (cudaError_t e = encode_map(&omap, a.out, na, a.nr, kDirectCols, kSdRows, true)) return e;
   const int chunks = na / kSdRows;
   const int split = chunks >= 8 ? chunks / 8 : 1;
   const dim3 grid(a.nr / kDirectCols, split);
   const int per = chunks / split;
   switch (na) {
-    case 256: k_sparse_dft<256><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
-    case 512: k_sparse_dft<512><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
-    case 1024: k_sparse_dft<1024><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
-    case 2048: k_sparse_dft<2048><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
-    case 4096: k_sparse_dft<4096><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
-    case 8192: k_sparse_dft<8192><<<grid, kSdThreads, 0, s>>>(a, col_tile, per); break;
+#define CSAR_SD(NA) \
+  case NA: k_sparse_dft<NA><<<grid, kSdThreads, kSdSmem, s>>>(omap, a, col_tile, per); break;
+    CSAR_SD(256) CSAR_SD(512) CSAR_SD(1024) CSAR_SD(2048) CSAR_SD(4096) CSAR_SD(8192)
+#undef CSAR_SD
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
