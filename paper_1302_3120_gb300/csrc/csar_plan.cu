@@ -588,6 +588,20 @@ cudaError_t enqueue_if(cudaStream_t s, cudaStream_t aux, cudaGraphConditionalHan
   return e != cudaSuccess ? e : e2;
 }
 
+// F_a of a sparse iterate into a.out: the direct DFT of the column groups with few
+// entries, then the clustered FFT of the others.  When captured, the FFT launch is the
+// body of an IF node that the direct DFT sets only if some group needs it (in the
+// steady state none does: the launch of ~2000 early-exiting clusters is skipped).
+cudaError_t sparse_forward(csar_plan plan, ColArgs a, cudaStream_t s) {
+  const int na = plan->na;
+  if (capturing(s) && sparse_dft_applies(na, plan->nr)) LK(capture_handle(s, &a.h_dense));
+  LK(launch_sparse_dft(na, a, plan->col_tile, s));
+  const cudaGraphConditionalHandle h = a.h_dense;
+  a.h_dense = 0;
+  return enqueue_if(s, plan->cond_stream, h,
+                    [&](cudaStream_t q) { return launch_col(na, plan->col, COL_SPARSE_FWD, a, plan->n_tiles, q); });
+}
+
 // One ITA iteration reading the sparse iterate in list `cur` and writing list 1-cur.
 // Optional per-pass events (profiling): ev[0..kPasses].
 constexpr int kPasses = 6;  // C1, R1, C2, R2, C3, selection+threshold
@@ -621,8 +635,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
   LK(mark(0));
   // G(X): F_a of the sparse iterate, range pass with conj(H3), conj(H2), conj(H1)
   c.out = b.z;
-  LK(launch_sparse_dft(na, c, plan->col_tile, s));
-  LK(launch_col(na, plan->col, COL_SPARSE_FWD, c, nt, s));
+  LK(sparse_forward(plan, c, s));
   LK(mark(1));
   LK(range_pass(plan, row_args(plan, b.z, plan->coef_g), true, s));
   LK(mark(2));
@@ -677,8 +690,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[cur];
     g.xs_val = b.dx;
     g.out = b.z;
-    LK(launch_sparse_dft(na, g, plan->col_tile, s));
-    LK(launch_col(na, plan->col, COL_SPARSE_FWD, g, nt, s));
+    LK(sparse_forward(plan, g, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 0u;
@@ -717,8 +729,7 @@ cudaError_t enqueue_iteration(csar_plan plan, const float2* y, int cur, const cs
     g.xs_idx = b.idx[nxt];
     g.xs_val = b.val[nxt];
     g.out = b.z;
-    LK(launch_sparse_dft(na, g, plan->col_tile, s));
-    LK(launch_col(na, plan->col, COL_SPARSE_FWD, g, nt, s));
+    LK(sparse_forward(plan, g, s));
     RowArgs r = row_args(plan, b.z, plan->coef_g);
     r.gate = g.gate;
     r.gate_val = 1u;

@@ -137,6 +137,9 @@ struct ColArgs {
   uint32_t gate_val;
   int nr;                   // row length N_r
   float scale;              // 1/N_a for inverse transforms
+  // k_sparse_dft: conditional handle (captured graphs) set to 1 when a column group is
+  // left to the FFT path, whose launch is then the body of an IF node (0: not captured)
+  cudaGraphConditionalHandle h_dense;
 };
 
 struct RowArgs {
@@ -231,6 +234,7 @@ ColConf col_conf_persist(int na);       // persistent passes: clusters of N_a/10
 cudaError_t launch_col(int na, ColConf conf, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);
+bool sparse_dft_applies(int na, int nr);
 cudaError_t sparse_dft_set_attributes(int na);
 // Tensor map (cuTensorMapEncodeTiled) of an [na][nr] complex64 array with boxes of
 // box_cols x box_rows (col_dispatch.cu); the map is named by its struct tag so that this

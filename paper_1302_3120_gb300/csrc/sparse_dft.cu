@@ -52,7 +52,10 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(const __grid_constant
   const int b1 = (grp + 1) * bpg < n_buckets ? (grp + 1) * bpg : n_buckets;
   const uint32_t e0 = a.xs_off[grp * bpg], e1 = a.xs_off[b1];
   const int ne = (int)(e1 - e0);
-  if (ne > kDirectMaxEntries) return;         // FFT path
+  if (ne > kDirectMaxEntries) {               // FFT path
+    if (threadIdx.x == 0 && a.h_dense) cudaGraphSetConditional(a.h_dense, 1u);
+    return;
+  }
   const int tid = threadIdx.x;
   load_twiddles(tw, a.tw);
   const int col0 = grp * kDirectCols;
@@ -144,8 +147,10 @@ cudaError_t sparse_dft_set_attributes(int na) {
   }
 }
 
+bool sparse_dft_applies(int na, int nr) { return nr >= kDirectCols && na >= kSdRows; }
+
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s) {
-  if (a.nr < kDirectCols || na < kSdRows) return cudaSuccess;   // small grids: FFT path only
+  if (!sparse_dft_applies(na, a.nr)) return cudaSuccess;   // small grids: FFT path only
   CUtensorMap omap;
   if (cudaError_t e = encode_map(&omap, a.out, na, a.nr, kDirectCols, kSdRows, true)) return e;
   const int chunks = na / kSdRows;
