@@ -73,6 +73,35 @@ __device__ __forceinline__ float2 shrink(float2 b, float sigma, int kind) {
   return make_float2(b.x * f, b.y * f);
 }
 
+// Inclusive scan of one value per thread over the kSelThreads threads of the block
+// (prefix: the sum over threads <= tid; suffix: over threads >= tid): a shuffle scan in
+// each warp, then one over the 32 warp totals.  ws: 64 shared words; two barriers; every
+// thread must call it.  Integer sums, so the result does not depend on the order.
+template <bool SUFFIX>
+__device__ __forceinline__ unsigned long long block_scan(unsigned long long v, unsigned long long* ws) {
+  static_assert(kSelThreads == 1024, "32 warps");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long n = SUFFIX ? __shfl_down_sync(0xffffffffu, v, o) : __shfl_up_sync(0xffffffffu, v, o);
+    if (SUFFIX ? lane + o < 32 : lane >= o) v += n;
+  }
+  if (lane == (SUFFIX ? 0 : 31)) ws[wid] = v;   // the warp's total
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long t = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long n = SUFFIX ? __shfl_down_sync(0xffffffffu, t, o) : __shfl_up_sync(0xffffffffu, t, o);
+      if (SUFFIX ? lane + o < 32 : lane >= o) t += n;
+    }
+    ws[32 + lane] = t;
+  }
+  __syncthreads();
+  if (SUFFIX) return v + (wid + 1 < 32 ? ws[32 + wid + 1] : 0ull);
+  return v + (wid > 0 ? ws[32 + wid - 1] : 0ull);
+}
+
 // Whole-block search, h[0..nb) with nb a multiple of 1024 or nb <= 1024:
 // largest bin b with S(b) = sum_{i >= b} h[i] >= target; *above = S(b+1).
 // Returns -1 if S(0) < target.  Uses sh (>= 1024 u64).  All threads get the result.
@@ -86,18 +115,9 @@ __device__ int find_bin(const uint32_t* h, int nb, uint64_t target, uint64_t* ab
   unsigned long long cs = 0;
   if (lo < nb)
     for (int i = 0; i < per; ++i) cs += h[lo + i];
-  sh[tid] = cs;
   if (tid == 0) { res_b = -1; res_above = 0; }
-  __syncthreads();
-  // inclusive suffix scan over sh[0..1024)
-  for (int off = 1; off < kSelThreads; off <<= 1) {
-    const unsigned long long add = (tid + off < kSelThreads) ? sh[tid + off] : 0ull;
-    __syncthreads();
-    sh[tid] += add;
-    __syncthreads();
-  }
-  const unsigned long long suf = sh[tid];                                   // S(lo)
-  const unsigned long long nxt = tid + 1 < kSelThreads ? sh[tid + 1] : 0ull;  // S(lo+per)
+  const unsigned long long suf = block_scan<true>(cs, sh);   // S(lo)
+  const unsigned long long nxt = suf - cs;                   // S(lo+per)
   if (lo < nb && suf >= target && nxt < target) {
     unsigned long long acc = nxt;
     for (int i = per - 1; i >= 0; --i) {
@@ -168,13 +188,8 @@ __device__ bool union_suffices(const SelArgs& a, unsigned long long* sh) {
   }
   for (int i = (int)(cut_hi >> kHistShift) + 1 + tid; i < (int)kHistBins; i += kSelThreads) cnt += a.hist[i];
   __syncthreads();
-  sh[tid] = cnt;
-  __syncthreads();
-  for (int off = kSelThreads / 2; off > 0; off >>= 1) {
-    if (tid < off) sh[tid] += sh[tid + off];
-    __syncthreads();
-  }
-  const bool ok = sh[0] >= (unsigned long long)a.K + 1;
+  block_scan<false>(cnt, sh);
+  const bool ok = sh[63] >= (unsigned long long)a.K + 1;   // the block's total
   __syncthreads();
   return ok;
 }
@@ -335,15 +350,8 @@ __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
   unsigned long long s = 0;
   for (int i = 0; i < per; ++i)
     if (lo + i < a.n_tiles) s += a.tile_cnt[lo + i];
-  sh[tid] = s;
-  __syncthreads();
-  for (int off = 1; off < kSelThreads; off <<= 1) {   // inclusive prefix scan
-    const unsigned long long add = tid >= off ? sh[tid - off] : 0ull;
-    __syncthreads();
-    sh[tid] += add;
-    __syncthreads();
-  }
-  unsigned long long run = tid ? sh[tid - 1] : 0ull;
+  const unsigned long long incl = block_scan<false>(s, sh);
+  unsigned long long run = incl - s;
   for (int i = 0; i < per; ++i) {
     const int k = lo + i;
     if (k < a.n_tiles) {
@@ -354,8 +362,8 @@ __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
     }
   }
   if (tid == kSelThreads - 1) {
-    a.xo_off[a.n_tiles] = (uint32_t)sh[kSelThreads - 1];
-    a.ctl->nnz = (uint32_t)sh[kSelThreads - 1];
+    a.xo_off[a.n_tiles] = (uint32_t)incl;
+    a.ctl->nnz = (uint32_t)incl;
   }
 }
 
@@ -473,15 +481,9 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
   unsigned long long run = 0;
   for (int i = 0; i < per; ++i)
     if (lo + i < nt) run += tcnt[lo + i];
-  sh[tid] = run;
-  __syncthreads();
-  for (int off = 1; off < kSelThreads; off <<= 1) {
-    const unsigned long long add = tid >= off ? sh[tid - off] : 0ull;
-    __syncthreads();
-    sh[tid] += add;
-    __syncthreads();
-  }
-  run = tid ? sh[tid - 1] : 0ull;
+  const unsigned long long incl = block_scan<false>(run, sh);
+  const uint32_t total = (uint32_t)sh[63];   // the last warp's inclusive prefix
+  run = incl - run;
   for (int i = 0; i < per; ++i) {
     const int k = lo + i;
     if (k < nt) {
@@ -491,7 +493,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
       run += cnt;
     }
   }
-  const uint32_t total = (uint32_t)sh[kSelThreads - 1];
   if (tid == 0) a.xo_off[nt] = total;
   __syncthreads();
   const uint32_t jstar = s_jstar;
