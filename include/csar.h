@@ -96,6 +96,15 @@ typedef struct csar_batch_s* csar_batch;
  * the autotuner chose.  Results are the same either way; only speed differs. */
 #define CSAR_PLAN_COL_PERSIST ((uint32_t)1 << 19)
 #define CSAR_PLAN_COL_NO_PERSIST ((uint32_t)1 << 20)
+/* csar_plan_create flag: configure the plan exactly as a member of a batch whose passes
+ * run as one launch each (csar_batch_create): column passes on 4096 values per CTA with
+ * 1 (n_az <= 1024), 2 (n_az = 2048) or 4 (n_az = 4096) CTAs per tile, the first column
+ * pass of the sparse iterate always by the clustered FFT (no direct DFT), the default
+ * range-pass schedule.  Only for n_az and n_rg in {512, 1024, 2048, 4096}
+ * (CSAR_E_UNSUPPORTED otherwise); not with the other CSAR_PLAN_COL_* flags
+ * (CSAR_E_INVALID).  A plan made so computes bit for bit what its batch computes for that
+ * patch. */
+#define CSAR_PLAN_BATCH_MEMBER ((uint32_t)1 << 21)
 
 /* csar_plan_create flag: csar_G / csar_M use the range-Doppler operator pair of the
  * paper's concrete example (Section III-C, Eqs. (14)-(18)) instead of the chirp-scaling
@@ -277,14 +286,21 @@ csar_status csar_echo_points(const csar_params* params, const int32_t* rows, con
 /* ---- Batches of independent patches (uneven sizes) -------------------------------- */
 
 /* One plan per patch (params[0..n_patches-1], each as for csar_plan_create with
- * `flags`).  Not thread-safe; the batch owns the plans. */
+ * `flags`).  When every patch has n_az and n_rg in {512, 1024, 2048, 4096} and `flags`
+ * holds no CSAR_PLAN_COL_* flag, the plans are made as batch members
+ * (CSAR_PLAN_BATCH_MEMBER) and the batch builds work tables of all patches' row blocks
+ * and column-tile groups (device memory, held until csar_batch_destroy).  Not
+ * thread-safe; the batch owns the plans. */
 csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint32_t flags,
                               csar_batch* out);
 csar_status csar_batch_destroy(csar_batch batch);
 
 /* Algorithm 1 on every patch together from X = 0: per iteration ONE CUDA graph launch
- * on `stream`, whose parallel branches are the patches' pass sequences, so patches of
- * different sizes run concurrently.  Y_dev, mask_dev, X_dev: host arrays of per-patch
+ * on `stream`.  For a batch of members with the fixed step, the graph holds one kernel
+ * launch per pass (and per selection kernel) over the work tables of all patches, each
+ * patch with its own K_p, sigma and control block; otherwise (NIHT step, other sizes or
+ * flags) its parallel branches are the patches' own pass sequences.  Either way patches
+ * of different sizes run concurrently.  Y_dev, mask_dev, X_dev: host arrays of per-patch
  * device pointers (layout as csar_solve); K: per-patch sparsity; opts: shared step,
  * threshold and iteration count (opts->K ignored). */
 csar_status csar_solve_batched(csar_batch batch, const void* const* Y_dev,

@@ -537,3 +537,6 @@ PLAN_RDA = 1 << 17
 # csar_plan_create flags: persistent, tensor-copy-fed column passes, or never
 PLAN_COL_PERSIST = 1 << 19
 PLAN_COL_NO_PERSIST = 1 << 20
+# csar_plan_create flag: the configuration of a member of a one-launch-per-pass batch
+# (bit-identical to what csar_solve_batched computes for that patch)
+PLAN_BATCH_MEMBER = 1 << 21

@@ -24,7 +24,7 @@ namespace csar {
   X(4096, 1, 4096) X(4096, 2, 4096) X(4096, 4, 4096) X(4096, 8, 4096)                          \
   X(2048, 1, 8192) X(2048, 2, 8192) X(2048, 4, 8192)                                           \
   X(2048, 1, 4096) X(2048, 2, 4096) X(2048, 4, 4096)                                           \
-  X(1024, 1, 8192) X(1024, 1, 4096) X(512, 1, 8192) X(256, 1, 8192) X(128, 1, 8192)            \
+  X(1024, 1, 8192) X(1024, 1, 4096) X(512, 1, 8192) X(512, 1, 4096) X(256, 1, 8192) X(128, 1, 8192)            \
   X(64, 1, 8192) X(32, 1, 8192) X(16, 1, 8192)
 #define CSAR_MASK_CONFIGS(X)                                                                  \
   X(8192, 1) X(8192, 2) X(8192, 4) X(8192, 8) X(8192, 16) X(4096, 1) X(4096, 2) X(4096, 4)     \

@@ -335,6 +335,8 @@ struct csar_plan_s {
   ColConf col_res;                // configuration of the residue and NIHT-norm passes (same W)
   int sel_fused_ok = 1;           // one-CTA selection allowed (CSAR_SEL_FUSED=0 disables it)
   int row_regs = 0;               // values per thread of the range passes (0: default 32; 16)
+  bool no_direct = false;         // batch member: the clustered FFT for every tile of C1
+  int buf_gen = 0;                // bumped whenever ensure_capacity reallocates
   int col_tile = 0, n_tiles = 0;
   RowCoef* coef_g = nullptr;
   RowCoef* coef_m = nullptr;
@@ -356,9 +358,21 @@ struct csar_plan_s {
 };
 
 // A batch of independent patches: one plan per patch; each ITA iteration of the whole
-// batch is one CUDA graph whose parallel branches are the patches' kernel sequences.
+// batch is one CUDA graph.  When every patch is a batch member (sizes the batched
+// kernels serve) and the step is fixed, the graph holds one launch per pass over a work
+// table of all patches' row blocks or tile groups (the patches' arguments in device
+// arrays); otherwise its parallel branches are the patches' own kernel sequences.
 struct csar_batch_s {
   std::vector<csar_plan> plans;
+  bool single = false;                       // one launch per pass
+  BatchItem* d_row_items = nullptr;          // row blocks of every patch
+  BatchItem* d_col_items = nullptr;          // tile groups of every patch
+  int n_row_items = 0, n_col_items = 0;
+  RowArgs* d_r1 = nullptr;                   // per patch: range pass of G, of M
+  RowArgs* d_r2 = nullptr;
+  ColArgs* d_c[2][4] = {};                   // per parity: C1, C2 / C3, re-pass 1, re-pass 2
+  SelArgs* d_sel[2] = {};                    // per parity
+  std::vector<int> key_gen;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
@@ -434,6 +448,7 @@ csar_status ensure_capacity(csar_plan plan, int64_t K, int iters) {
   const uint32_t want = (uint32_t)want64;
   if (b.cand_cap < want) {
     drop_graphs(plan);
+    ++plan->buf_gen;
     if (b.cand_idx) cudaFree(b.cand_idx);
     if (b.cand_val) cudaFree(b.cand_val);
     b.cand_idx = nullptr;
@@ -445,6 +460,7 @@ csar_status ensure_capacity(csar_plan plan, int64_t K, int iters) {
   }
   if (b.stats_cap < iters) {
     drop_graphs(plan);
+    ++plan->buf_gen;
     if (b.stats) cudaFree(b.stats);
     b.stats = nullptr;
     b.stats_cap = 0;
@@ -457,6 +473,7 @@ csar_status ensure_capacity(csar_plan plan, int64_t K, int iters) {
 
 ColArgs col_args(csar_plan plan) {
   ColArgs a{};
+  a.no_direct = plan->no_direct ? 1 : 0;
   a.tw = plan->tw;
   a.nr = plan->nr;
   a.ctl = plan->b.ctl;
@@ -594,6 +611,7 @@ cudaError_t enqueue_if(cudaStream_t s, cudaStream_t aux, cudaGraphConditionalHan
 // steady state none does: the launch of ~2000 early-exiting clusters is skipped).
 cudaError_t sparse_forward(csar_plan plan, ColArgs a, cudaStream_t s) {
   const int na = plan->na;
+  if (plan->no_direct) return launch_col(na, plan->col, COL_SPARSE_FWD, a, plan->n_tiles, s);
   if (capturing(s) && sparse_dft_applies(na, plan->nr)) LK(capture_handle(s, &a.h_dense));
   LK(launch_sparse_dft(na, a, plan->col_tile, s));
   const cudaGraphConditionalHandle h = a.h_dense;
@@ -977,8 +995,19 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (flags & ~(0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_RDA |
-                CSAR_PLAN_COL_PERSIST | CSAR_PLAN_COL_NO_PERSIST))
+                CSAR_PLAN_COL_PERSIST | CSAR_PLAN_COL_NO_PERSIST | CSAR_PLAN_BATCH_MEMBER))
     return fail(CSAR_E_INVALID, "unknown plan flags 0x%x", flags);
+  const bool member = (flags & CSAR_PLAN_BATCH_MEMBER) != 0;
+  if (member) {
+    if (flags & (0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_COL_PERSIST |
+                 CSAR_PLAN_COL_NO_PERSIST | CSAR_PLAN_RDA))
+      return fail(CSAR_E_INVALID, "CSAR_PLAN_BATCH_MEMBER with other column or operator flags");
+    if (!params) return fail(CSAR_E_INVALID, "params is NULL");
+    if (!batch_member_ok(params->n_az, params->n_rg))
+      return fail(CSAR_E_UNSUPPORTED, "batch member plans need n_az, n_rg in {512, 1024, 2048, 4096}");
+    flags |= CSAR_PLAN_COL_CLUSTER(batch_col_cluster(params->n_az)) | CSAR_PLAN_COL_HALF_TILE |
+             CSAR_PLAN_COL_NO_PERSIST;
+  }
   if ((flags & CSAR_PLAN_COL_PERSIST) && (flags & CSAR_PLAN_COL_NO_PERSIST))
     return fail(CSAR_E_INVALID, "CSAR_PLAN_COL_PERSIST with CSAR_PLAN_COL_NO_PERSIST");
   const uint32_t tile_flags = flags & (CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE);
@@ -1036,6 +1065,10 @@ csar_status csar_plan_create(const csar_params* params, uint32_t flags, csar_pla
   if (const char* sf = std::getenv("CSAR_SEL_FUSED")) plan->sel_fused_ok = sf[0] != '0';
   plan->row_regs = tuned_row_regs(plan->na, plan->nr);
   if (const char* rr = std::getenv("CSAR_ROW_REGS")) plan->row_regs = std::atoi(rr) == 16 ? 16 : 0;
+  if (member) {
+    plan->row_regs = 0;
+    plan->no_direct = true;
+  }
   const char* ng = std::getenv("CSAR_NO_GRAPH");
   plan->use_graphs = !(ng && ng[0] == '1');
   auto bail = [&](csar_status st) {
@@ -1426,16 +1459,134 @@ csar_status csar_af_backward(csar_plan plan, const void* Y_dev, const uint32_t* 
 // ---------------------------------------------------------------- batches
 csar_status csar_batch_destroy(csar_batch b);
 
+namespace {
+
+// Work tables of the one-launch-per-pass batch: every patch's row blocks (8192 values
+// each) and tile groups (one cluster each), patch by patch.
+csar_status batch_build_tables(csar_batch b) {
+  std::vector<BatchItem> ri, ci;
+  for (int i = 0; i < (int)b->plans.size(); ++i) {
+    const csar_plan p = b->plans[i];
+    const int blocks = p->na / row_w(p->nr);
+    for (int k = 0; k < blocks; ++k) ri.push_back(BatchItem{i, k, p->nr, 0});
+    const int per = batch_col_tiles_per_item(p->na);
+    const int units = (p->n_tiles + per - 1) / per;
+    for (int u = 0; u < units; ++u) ci.push_back(BatchItem{i, u, p->na, 0});
+  }
+  const size_t np = b->plans.size();
+  CK(dalloc(&b->d_row_items, ri.size()));
+  CK(dalloc(&b->d_col_items, ci.size()));
+  CK(cudaMemcpy(b->d_row_items, ri.data(), ri.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_col_items, ci.data(), ci.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+  b->n_row_items = (int)ri.size();
+  b->n_col_items = (int)ci.size();
+  CK(dalloc(&b->d_r1, np));
+  CK(dalloc(&b->d_r2, np));
+  for (int par = 0; par < 2; ++par) {
+    for (int k = 0; k < 4; ++k) CK(dalloc(&b->d_c[par][k], np));
+    CK(dalloc(&b->d_sel[par], np));
+  }
+  CK(row_batched_set_attributes());
+  CK(col_batched_set_attributes());
+  return CSAR_OK;
+}
+
+// The patches' pass arguments for this solve (buffers, step, threshold, K_p), as the
+// per-patch iteration forms them, into the batch's device arrays.
+csar_status batch_upload_args(csar_batch b, const int64_t* K, const csar_opts& o) {
+  const int np = (int)b->plans.size();
+  std::vector<RowArgs> r1(np), r2(np);
+  std::vector<ColArgs> c[2][4];
+  std::vector<SelArgs> sa[2];
+  for (int par = 0; par < 2; ++par) {
+    for (int k = 0; k < 4; ++k) c[par][k].resize(np);
+    sa[par].resize(np);
+  }
+  for (int i = 0; i < np; ++i) {
+    const csar_plan p = b->plans[i];
+    const Buffers& bb = p->b;
+    r1[i] = row_args(p, bb.z, p->coef_g);
+    r2[i] = row_args(p, bb.z, p->coef_m);
+    r2[i].yf = bb.yf;
+    r2[i].partial = bb.partial;
+    r2[i].ctl = bb.ctl;
+    r2[i].resid_scale = 1.0f / (float)p->na;
+    csar_opts oi = o;
+    oi.K = K[i];
+    for (int par = 0; par < 2; ++par) {
+      ColArgs a = col_args(p);
+      a.xs_off = bb.off[par];
+      a.xs_idx = bb.idx[par];
+      a.xs_val = bb.val[par];
+      a.out = bb.z;
+      c[par][0][i] = a;
+      a.in = bb.z;
+      a.mask = bb.mask_t;
+      c[par][1][i] = a;
+      a.gate_val = kRepassCut;
+      c[par][2][i] = a;
+      a.gate_val = kRepassCut2;
+      c[par][3][i] = a;
+      sa[par][i] = sel_args(p, par, oi);
+    }
+  }
+  CK(cudaMemcpy(b->d_r1, r1.data(), np * sizeof(RowArgs), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b->d_r2, r2.data(), np * sizeof(RowArgs), cudaMemcpyHostToDevice));
+  for (int par = 0; par < 2; ++par) {
+    for (int k = 0; k < 4; ++k)
+      CK(cudaMemcpy(b->d_c[par][k], c[par][k].data(), np * sizeof(ColArgs), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_sel[par], sa[par].data(), np * sizeof(SelArgs), cudaMemcpyHostToDevice));
+  }
+  return CSAR_OK;
+}
+
+// One ITA iteration of every patch (fixed step), reading list `par` of each: one launch
+// per pass and per selection kernel, whatever the number of patches.  The re-passes and
+// the two selection paths are decided per patch on the device (early exits), as in the
+// per-patch iteration outside a graph.
+cudaError_t enqueue_batched_iteration(csar_batch b, int par, cudaStream_t s) {
+  const int np = (int)b->plans.size();
+  const BatchItem* ci = b->d_col_items;
+  const int nci = b->n_col_items;
+  LK(launch_col_batched(COL_SPARSE_FWD, b->d_c[par][0], ci, nci, s));   // C1: F_a X
+  LK(launch_row_batched(false, b->d_r1, b->d_row_items, b->n_row_items, s));   // R1
+  LK(launch_col_batched(COL_RESID, b->d_c[par][1], ci, nci, s));        // C2: F_a(S.G X)
+  LK(launch_row_batched(true, b->d_r2, b->d_row_items, b->n_row_items, s));    // R2: M(r)
+  LK(launch_col_batched(COL_SELECT, b->d_c[par][1], ci, nci, s));       // C3: Delta X, histogram
+  const SelArgs* sa = b->d_sel[par];
+  LK(launch_sel_batched(SelKernel::kCheck, sa, np, 0, s));
+  LK(launch_col_batched(COL_REPASS, b->d_c[par][2], ci, nci, s));
+  LK(launch_sel_batched(SelKernel::kCheck2, sa, np, 0, s));
+  LK(launch_col_batched(COL_REPASS, b->d_c[par][3], ci, nci, s));
+  LK(launch_sel_batched(SelKernel::kFused, sa, np, 0, s));
+  for (int lev = 0; lev < 3; ++lev) {
+    LK(launch_sel_batched(SelKernel::kRound, sa, np, lev, s));
+    LK(launch_sel_batched(SelKernel::kPick, sa, np, lev, s));
+  }
+  LK(launch_sel_batched(SelKernel::kCount, sa, np, 0, s));
+  LK(launch_sel_batched(SelKernel::kScan, sa, np, 0, s));
+  LK(launch_sel_batched(SelKernel::kScatter, sa, np, 0, s));
+  return launch_sel_batched(SelKernel::kFinish, sa, np, 0, s);
+}
+
+}  // namespace
+
 csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint32_t flags, csar_batch* out) {
   if (!out) return fail(CSAR_E_INVALID, "out is NULL");
   *out = nullptr;
   if (!params || n_patches <= 0) return fail(CSAR_E_INVALID, "need n_patches > 0 parameter sets");
   if (flags & CSAR_PLAN_RDA) return fail(CSAR_E_UNSUPPORTED, "batches use the chirp-scaling operator pair");
+  // every patch a batch member (the sizes the batched kernels serve, no column flags):
+  // one launch per pass
+  bool single = !(flags & (0xff00u | CSAR_PLAN_COL_HALF_TILE | CSAR_PLAN_COL_WIDE_TILE | CSAR_PLAN_COL_PERSIST |
+                           CSAR_PLAN_COL_NO_PERSIST | CSAR_PLAN_BATCH_MEMBER));
+  for (int i = 0; single && i < n_patches; ++i) single = batch_member_ok(params[i].n_az, params[i].n_rg);
+  const uint32_t pflags = single ? (flags | CSAR_PLAN_BATCH_MEMBER) : flags;
   csar_batch b = new csar_batch_s();
   CK(cudaGetDevice(&b->dev));
   for (int i = 0; i < n_patches; ++i) {
     csar_plan p = nullptr;
-    if (csar_status st = csar_plan_create(&params[i], flags, &p)) {
+    if (csar_status st = csar_plan_create(&params[i], pflags, &p)) {
       csar_batch_destroy(b);
       return st;
     }
@@ -1457,6 +1608,13 @@ csar_status csar_batch_create(const csar_params* params, int32_t n_patches, uint
     csar_batch_destroy(b);
     return cuda_fail(ce, "csar_batch_create");
   }
+  if (single) {
+    if (csar_status st = batch_build_tables(b)) {
+      csar_batch_destroy(b);
+      return st;
+    }
+    b->single = true;
+  }
   *out = b;
   return CSAR_OK;
 }
@@ -1471,6 +1629,14 @@ csar_status csar_batch_destroy(csar_batch b) {
   for (auto e : b->join) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_row_items);
+  cudaFree(b->d_col_items);
+  cudaFree(b->d_r1);
+  cudaFree(b->d_r2);
+  for (int par = 0; par < 2; ++par) {
+    for (int k = 0; k < 4; ++k) cudaFree(b->d_c[par][k]);
+    cudaFree(b->d_sel[par]);
+  }
   for (auto p : b->plans) csar_plan_destroy(p);
   delete b;
   return CSAR_OK;
@@ -1499,22 +1665,28 @@ csar_status csar_solve_batched(csar_batch b, const void* const* Y_dev, const uin
     k_ctl_init<<<1, 1, 0, s>>>(p->b.ctl, 0u, p->b.off[0], p->n_tiles);
     CK(cudaGetLastError());
   }
-  // one graph per parity: fork to the patches' streams, one branch per patch, join
+  // one graph per parity: one launch per pass over all patches (batch members, fixed
+  // step), or a fork to the patches' streams with one branch per patch and a join
+  const bool single = b->single && o.mu_mode == CSAR_MU_FIXED;
   bool same = (int)b->key_y.size() == np && b->key_o.mu_mode == o.mu_mode && b->key_o.mu == o.mu &&
-              b->key_o.thresh == o.thresh;
-  for (int i = 0; same && i < np; ++i) same = b->key_y[i] == Y_dev[i] && b->key_k[i] == K[i];
+              b->key_o.thresh == o.thresh && (int)b->key_gen.size() == np;
+  for (int i = 0; same && i < np; ++i)
+    same = b->key_y[i] == Y_dev[i] && b->key_k[i] == K[i] && b->key_gen[i] == b->plans[i]->buf_gen;
   if (!same) {
     for (int par = 0; par < 2; ++par) {
       if (b->exec[par]) cudaGraphExecDestroy(b->exec[par]);
       b->exec[par] = nullptr;
     }
+    if (single)
+      if (csar_status st = batch_upload_args(b, K, o)) return st;
   }
   for (int par = 0; par < 2 && o.iters > 0; ++par) {
     if (b->exec[par]) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaEventRecord(b->fork, b->cap);
-    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    if (single && e == cudaSuccess) e = enqueue_batched_iteration(b, par, b->cap);
+    for (int i = 0; !single && i < np && e == cudaSuccess; ++i) {
       csar_opts oi = o;
       oi.K = K[i];
       e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
@@ -1534,6 +1706,8 @@ csar_status csar_solve_batched(csar_batch b, const void* const* Y_dev, const uin
   b->key_y.assign(Y_dev, Y_dev + np);
   b->key_k.assign(K, K + np);
   b->key_o = o;
+  b->key_gen.resize(np);
+  for (int i = 0; i < np; ++i) b->key_gen[i] = b->plans[i]->buf_gen;
   int cur = 0;
   for (int it = 0; it < o.iters; ++it) {
     CK(cudaGraphLaunch(b->exec[cur], s));

@@ -140,7 +140,22 @@ struct ColArgs {
   // k_sparse_dft: conditional handle (captured graphs) set to 1 when a column group is
   // left to the FFT path, whose launch is then the body of an IF node (0: not captured)
   cudaGraphConditionalHandle h_dense;
+  // COL_SPARSE_FWD: transform every tile, also those the direct DFT would take (batches)
+  int no_direct;
 };
+
+// One unit of work of a batched pass: row block or column-tile group `unit` of patch
+// `patch`, whose transform length along the pass is n.
+struct BatchItem {
+  int patch;
+  int unit;
+  int n;
+  int pad;
+};
+// Row lengths and azimuth lengths the batched passes serve (other patch sizes take the
+// per-patch graph branches).
+#define CSAR_BATCH_ROW_SIZES(X) X(512) X(1024) X(2048) X(4096)
+#define CSAR_BATCH_COL_SIZES(X) X(512) X(1024) X(2048) X(4096)
 
 struct RowArgs {
   float2* data;             // output (and input unless src is set), [n_rows][N_r]
@@ -234,6 +249,17 @@ ColConf col_conf_persist(int na);       // persistent passes: clusters of N_a/10
 cudaError_t launch_col(int na, ColConf conf, ColMode mode, const ColArgs& a, int n_tiles, cudaStream_t s);
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sparse_dft(int na, const ColArgs& a, int col_tile, cudaStream_t s);
+cudaError_t row_batched_set_attributes();
+// Batched column passes (col_batched.cu): CTAs per tile for azimuth length na (0: na is
+// not served), tiles per work item, attributes, one launch over all work items.
+int batch_col_cluster(int na);
+bool batch_member_ok(int na, int nr);
+int batch_col_tiles_per_item(int na);
+cudaError_t col_batched_set_attributes();
+cudaError_t launch_col_batched(ColMode mode, const ColArgs* args, const BatchItem* items, int n_items,
+                               cudaStream_t s);
+cudaError_t launch_row_batched(bool resid, const RowArgs* args, const BatchItem* items, int n_items,
+                               cudaStream_t s);
 bool sparse_dft_applies(int na, int nr);
 cudaError_t sparse_dft_set_attributes(int na);
 // Tensor map (cuTensorMapEncodeTiled) of an [na][nr] complex64 array with boxes of
@@ -311,6 +337,8 @@ cudaError_t launch_thr_scatter_mode(const SelArgs& a, int raw, cudaStream_t s);
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s);
 cudaError_t launch_sel_finish(const SelArgs& a, cudaStream_t s);
+enum class SelKernel { kCheck, kCheck2, kRound, kPick, kCount, kScan, kScatter, kFused, kFinish };
+cudaError_t launch_sel_batched(SelKernel k, const SelArgs* as, int np, int arg, cudaStream_t s);
 cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s);
 cudaError_t launch_row_rda(int nr, const RdaArgs& a, bool is_g, cudaStream_t s);
 cudaError_t rda_set_attributes(int nr);

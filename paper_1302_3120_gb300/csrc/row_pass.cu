@@ -41,140 +41,43 @@ __host__ __device__ constexpr int row_threads_r(int n, int r) { return n * row_w
 // carries none of its code.  R: values per thread, which sets the radix schedule of the
 // transforms (R = 32: 8192 = 8 x 32 x 32, two exchanges; R = 16: 2 x 16 x 16 x 16, three
 // exchanges and twice the threads per row); the plan chooses (autotuner, CSAR_ROW_REGS).
+// Block index of a CTA: the grid's own (read from the special register where it is
+// used, which keeps it out of the register file) or a batch item's.
+struct BlkOfGrid {
+  __device__ __forceinline__ int operator()() const { return (int)blockIdx.x; }
+};
+struct BlkOfItem {
+  int b;
+  __device__ __forceinline__ int operator()() const { return b; }
+};
+
+template <int N, bool RESID, int R, class BLK>
+__device__ __forceinline__ void row_body(const RowArgs& a, BLK blk) {
+#include "row_body.inc"
+}
+
+// The per-pass kernel carries the statements itself (see col_pass.cuh): the hot passes
+// keep their register allocation.
 template <int N, bool RESID, int R = regs_for(N)>
 __global__ void __launch_bounds__(row_threads_r(N, R), 2) k_row(RowArgs a) {
-  constexpr int WR = row_w(N);
-  constexpr int QR = N / R;
-  constexpr int NTR = row_threads_r(N, R);
-  using L = Layout<N, WR, false>;
-  extern __shared__ float2 smem[];
-  if (a.gate && *a.gate != a.gate_val) return;
-  float2* sm = smem;
-  float2* tw = smem + L::kSmemElems;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tw + kTwLo + kTwHi + 16);   // after 32 floats of reduction scratch
-  float2* gam = tw + kTwLo + kTwHi + 18;
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * WR;
-  if (RESID && kBulkY<N> && tid == 0) {
-    // rows row0 .. row0 + live_rows - 1 of F_a(S.Y) into the exchange buffer, plain order
-    const int live_rows = a.n_rows - row0 < WR ? a.n_rows - row0 : WR;
-    const uint32_t mb = smem_addr(mbar);
-    mbar_init(mb, 1u);
-    bulk_load_armed(smem_addr(sm), a.yf + (size_t)row0 * N, (uint32_t)(live_rows * N * sizeof(float2)), mb);
-  }
-  load_twiddles(tw, a.tw);
-  const int w = tid / QR, t = tid % QR;
-  const int row = row0 + w;
-  const bool live = row < a.n_rows;
-  const RowCoef* cp = a.coef + (live ? row : 0);
-  float2* rp = a.data + (size_t)(live ? row : 0) * N;
-  const float2* sp = a.src ? a.src + (size_t)(live ? row : 0) * N : rp;
-  float2 v[R];
-  const bool ok_row = !live || CSAR_CHECK((size_t)row * N + (N - 1), (size_t)a.n_rows * N, a.ctl);
-#pragma unroll
-  for (int s = 0; s < R; ++s) v[s] = live && ok_row ? __ldcs(&sp[t + s * QR]) : make_float2(0.f, 0.f);
-  if constexpr (kRowChains<N>) {
-    // Gamma tables of this CTA's rows for the three phases: gam[(row*3 + phase)*R + u]
-    for (int i = tid; i < WR * 3 * R; i += NTR) {
-      const int rw = blockIdx.x * WR + i / (3 * R);
-      const RowCoef& rc = a.coef[rw < a.n_rows ? rw : 0];
-      const int ph = (i / R) % 3;
-      gam[i] = phase_gamma(ph == 0 ? rc.pro : (ph == 1 ? rc.mid : rc.epi), QR, i % R);
-    }
-    __syncthreads();
-  }
-  const float2* gw = gam + w * 3 * R;
-  if constexpr (RESID) {
-    // residue form: v = F_a(S.Y) - v, its squared norm and a finiteness check
-    float acc = 0.f;
-    bool bad = false;
-    if constexpr (kBulkY<N>) {
-      const uint32_t mb = smem_addr(mbar);   // initialised before the Gamma-table barrier
-      bool landed = mbar_wait_for(mb, 0u, 1000000000ull);
-      if (!landed) {
-        // the copy did not land within a second: report it, and give it one more second
-        atomicOr(&a.ctl->err, kErrTimeout);
-        landed = mbar_wait_for(mb, 0u, 1000000000ull);
-      }
-      // if any thread still saw no completion, the whole CTA leaves without touching the
-      // buffer again (the latched error marks the result invalid)
-      if (__syncthreads_or(!landed)) return;
-      const float2* ys = sm + w * N;
-#pragma unroll
-      for (int s = 0; s < R; ++s) {
-        const float2 y = live ? ys[t + s * QR] : make_float2(0.f, 0.f);
-        v[s] = csub(y, v[s]);
-        acc += cabs2(v[s]);
-        bad |= !(isfinite(v[s].x) && isfinite(v[s].y));
-      }
-    } else {
-      const float2* yp = a.yf + (size_t)(live ? row : 0) * N;
-      constexpr int kG = R >= 8 ? 8 : R;   // loads in flight per group (register pressure)
-#pragma unroll
-      for (int g0 = 0; g0 < R; g0 += kG) {
-        float2 y[kG];
-#pragma unroll
-        for (int j = 0; j < kG; ++j) y[j] = live ? __ldcs(&yp[t + (g0 + j) * QR]) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < kG; ++j) {
-          v[g0 + j] = csub(y[j], v[g0 + j]);
-          acc += cabs2(v[g0 + j]);
-          bad |= !(isfinite(v[g0 + j].x) && isfinite(v[g0 + j].y));
-        }
-      }
-    }
-    if (bad) atomicOr(&a.ctl->err, kErrNonfinite);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    float* red = reinterpret_cast<float*>(tw + kTwLo + kTwHi);
-    constexpr int kWarps = NTR / 32;
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      float tot = 0.f;
-#pragma unroll
-      for (int i = 0; i < kWarps; ++i) tot += red[i];
-      a.partial[blockIdx.x] = tot * a.resid_scale;
-    }
-  }
-  if constexpr (kRowChains<N>) {
-    phase_chain<R, 0, R>(v, cp->pro, t - N / 2, QR, 1.f, gw);
-  } else {
-    const PhaseCoef c = cp->pro;
-    phase_ap<R, 0, R>(v, c, t - N / 2, QR, 1.f, phase_second_diff(c, QR));
-  }
-  // The range IFFT runs as the forward FFT of the conjugate (unnormalised IFFT(u) =
-  // conj(FFT(conj(u))); conjugation commutes exactly with every rounded operation, so
-  // the result is the same), which lets one copy of the FFT code serve both transforms
-  // in a rolled loop: half the instruction footprint of two unrolled transforms.
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    fft<N, false, L, false, R>(v, sm, tw, t, w);
-    if (pass == 1) break;
-    // range-frequency bin of v[s]: t + s*QR for s < R/2, t + (s - R)*QR above
-    if constexpr (kRowChains<N>) {
-      phase_chain<R, 0, R / 2>(v, cp->mid, t, QR, 1.f, gw + R);
-      phase_chain<R, R / 2, R>(v, cp->mid, t - (R / 2) * QR, QR, 1.f, gw + R);
-    } else {
-      const PhaseCoef c = cp->mid;
-      const float2 dd = phase_second_diff(c, QR);
-      phase_ap<R, 0, R / 2>(v, c, t, QR, 1.f, dd);
-      phase_ap<R, R / 2, R>(v, c, t - (R / 2) * QR, QR, 1.f, dd);
-    }
-#pragma unroll
-    for (int s = 0; s < R; ++s) v[s].y = -v[s].y;
-  }
-#pragma unroll
-  for (int s = 0; s < R; ++s) v[s].y = -v[s].y;
-  if constexpr (kRowChains<N>) {
-    phase_chain<R, 0, R>(v, cp->epi, t - N / 2, QR, a.scale, gw + 2 * R);
-  } else {
-    const PhaseCoef c = cp->epi;
-    phase_ap<R, 0, R>(v, c, t - N / 2, QR, a.scale, phase_second_diff(c, QR));
-  }
-  if (live && ok_row) {
-#pragma unroll
-    for (int s = 0; s < R; ++s) __stcs(&rp[t + s * QR], v[s]);
+  const BlkOfGrid blk{};
+#include "row_body.inc"
+}
+
+// Range passes of a batch of patches in one launch: CTA i runs row block items[i].unit of
+// patch items[i].patch (row length items[i].n) with that patch's arguments.  Every row
+// length runs 256 threads on 8192 values, so one launch serves every patch size.
+template <bool RESID>
+__global__ void __launch_bounds__(256, 2) k_row_batched(const RowArgs* __restrict__ args,
+                                                        const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const RowArgs a = args[it.patch];
+  switch (it.n) {
+#define CSAR_CASE(N) \
+  case N: row_body<N, RESID, regs_for(N)>(a, BlkOfItem{it.unit}); break;
+    CSAR_BATCH_ROW_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+    default: break;
   }
 }
 
@@ -223,6 +126,31 @@ cudaError_t row_set_attributes(int nr) {
 #undef CSAR_CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+static size_t row_batched_smem() {
+  size_t m = 0;
+#define CSAR_CASE(N) m = row_smem<N, regs_for(N)>() > m ? row_smem<N, regs_for(N)>() : m;
+  CSAR_BATCH_ROW_SIZES(CSAR_CASE)
+#undef CSAR_CASE
+  return m;
+}
+
+cudaError_t row_batched_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_row_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)row_batched_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_row_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)row_batched_smem());
+  return e;
+}
+
+cudaError_t launch_row_batched(bool resid, const RowArgs* args, const BatchItem* items, int n_items,
+                               cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  if (resid) k_row_batched<true><<<n_items, 256, row_batched_smem(), s>>>(args, items);
+  else k_row_batched<false><<<n_items, 256, row_batched_smem(), s>>>(args, items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_row(int nr, const RowArgs& a, cudaStream_t s) {

@@ -194,7 +194,7 @@ __device__ bool union_suffices(const SelArgs& a, unsigned long long* sh) {
   return ok;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
+__device__ __forceinline__ void sel_check_body(const SelArgs& a) {
   __shared__ unsigned long long sh[kSelThreads];
   __shared__ uint32_t state;
   Ctl* c = a.ctl;
@@ -244,9 +244,14 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) {
     check_capacity(a, b > 0 ? b : (int)(kMinKey >> kHistShift));
   }
 }
+__global__ void __launch_bounds__(kSelThreads) k_sel_check(SelArgs a) { sel_check_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_sel_check_b(const SelArgs* __restrict__ as) {
+  sel_check_body(as[blockIdx.y]);
+}
 
 // After a full-histogram re-pass: the exact cut, and the second (candidate) re-pass.
-__global__ void __launch_bounds__(kSelThreads) k_sel_check2(SelArgs a) {
+__device__ __forceinline__ void sel_check2_body(const SelArgs& a) {
   __shared__ unsigned long long sh[kSelThreads];
   Ctl* c = a.ctl;
   if (c->need_repass != kRepassHist) return;   // uniform
@@ -261,9 +266,14 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_check2(SelArgs a) {
     check_capacity(a, b > 0 ? b : (int)(kMinKey >> kHistShift));
   }
 }
+__global__ void __launch_bounds__(kSelThreads) k_sel_check2(SelArgs a) { sel_check2_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_sel_check2_b(const SelArgs* __restrict__ as) {
+  sel_check2_body(as[blockIdx.y]);
+}
 
 // ------------------------------------------------------------------ radix select
-__global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level) {
+__device__ __forceinline__ void sel_round_body(const SelArgs& a, int level) {
   __shared__ uint32_t h[kHistBins];
   const Ctl* c = a.ctl;
   if (c->sel_fused || c->sel_prefix == 0xffffffffu) return;   // fused path, or decided
@@ -289,8 +299,13 @@ __global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level
   for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x)
     if (h[i]) atomicAdd(&a.hist2[i], h[i]);
 }
+__global__ void __launch_bounds__(kGridThreads) k_sel_round(SelArgs a, int level) { sel_round_body(a, level); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kGridThreads) k_sel_round_b(const SelArgs* __restrict__ as, int level) {
+  sel_round_body(as[blockIdx.y], level);
+}
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) {
+__device__ __forceinline__ void sel_pick_body(const SelArgs& a, int level) {
   __shared__ unsigned long long sh[kSelThreads];
   Ctl* c = a.ctl;
   if (c->sel_fused) return;                   // uniform: the one-CTA kernel selects
@@ -323,11 +338,16 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) 
   __syncthreads();
   for (int i = threadIdx.x; i < (int)kHistBins; i += blockDim.x) a.hist2[i] = 0u;
 }
+__global__ void __launch_bounds__(kSelThreads) k_sel_pick(SelArgs a, int level) { sel_pick_body(a, level); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_sel_pick_b(const SelArgs* __restrict__ as, int level) {
+  sel_pick_body(as[blockIdx.y], level);
+}
 
 // ------------------------------------------------------------------ threshold
 __device__ __forceinline__ bool kept(uint32_t key, uint32_t s2) { return key > s2 && key >= kMinKey; }
 
-__global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
+__device__ __forceinline__ void thr_count_body(const SelArgs& a) {
   Ctl* c = a.ctl;
   if (c->sel_fused) return;
   const uint32_t nx = c->nx, nu = union_size(c, a.cand_cap), s2 = c->sigma2_key;
@@ -339,9 +359,14 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) {
     else if (key == s2 && s2 >= kMinKey) atomicMin(&c->jstar, idx);   // the (K+1)-th element
   }
 }
+__global__ void __launch_bounds__(kGridThreads) k_thr_count(SelArgs a) { thr_count_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kGridThreads) k_thr_count_b(const SelArgs* __restrict__ as) {
+  thr_count_body(as[blockIdx.y]);
+}
 
 // Exclusive scan of the per-tile counts into the next iterate's offsets.
-__global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
+__device__ __forceinline__ void thr_scan_body(const SelArgs& a) {
   __shared__ unsigned long long sh[kSelThreads];
   if (a.ctl->sel_fused) return;
   const int tid = threadIdx.x;
@@ -366,9 +391,14 @@ __global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) {
     a.ctl->nnz = (uint32_t)incl;
   }
 }
+__global__ void __launch_bounds__(kSelThreads) k_thr_scan(SelArgs a) { thr_scan_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_thr_scan_b(const SelArgs* __restrict__ as) {
+  thr_scan_body(as[blockIdx.y]);
+}
 
 // raw != 0: store b itself (the NIHT support list of the first iteration).
-__global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw) {
+__device__ __forceinline__ void thr_scatter_body(const SelArgs& a, int raw) {
   Ctl* c = a.ctl;
   if (c->sel_fused) return;
   raw = raw && c->niht_first;
@@ -387,6 +417,11 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw
     a.xo_val[pos] = raw ? b : shrink(b, sigma, a.thresh);
   }
 }
+__global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw) { thr_scatter_body(a, raw); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kGridThreads) k_thr_scatter_b(const SelArgs* __restrict__ as, int raw) {
+  thr_scatter_body(as[blockIdx.y], raw);
+}
 
 // ------------------------------------------------------------------ one-CTA selection
 // The radix select, the per-tile count, its scan and the scatter of k_sel_round /
@@ -395,7 +430,7 @@ __global__ void __launch_bounds__(kGridThreads) k_thr_scatter(SelArgs a, int raw
 // candidates) has at most kFusedMaxUnion elements, the step is fixed and no re-pass ran.
 constexpr size_t kFusedSmem = (size_t)(kFusedMaxUnion + kHistBins + kFusedMaxTiles) * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
+__device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
   extern __shared__ uint32_t fsm[];
   uint32_t* key = fsm;                        // union keys
   uint32_t* h = key + kFusedMaxUnion;         // radix histogram
@@ -527,6 +562,11 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) {
     c->nnz = total;
   }
 }
+__global__ void __launch_bounds__(kSelThreads) k_sel_fused(SelArgs a) { sel_fused_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_sel_fused_b(const SelArgs* __restrict__ as) {
+  sel_fused_body(as[blockIdx.y]);
+}
 
 // NIHT: mu = ||Delta X_Gamma||^2 / ||S . G(Delta X_Gamma)||^2 (den from the column
 // pass partials).  first != 0: Gamma is the new list (values = Delta X, first
@@ -570,7 +610,7 @@ __global__ void __launch_bounds__(kSelThreads) k_niht_mu(SelArgs a, int first) {
 }
 
 // Statistics, next cut guess and counter resets (after the scatter).
-__global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
+__device__ __forceinline__ void sel_finish_body(const SelArgs& a) {
   __shared__ double sd[kSelThreads];
   Ctl* c = a.ctl;
   const int tid = threadIdx.x;
@@ -615,6 +655,11 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) {
     c->sel_prefix = 0u;
     c->jstar = 0xffffffffu;
   }
+}
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish(SelArgs a) { sel_finish_body(a); }
+// batched: patch blockIdx.y
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish_b(const SelArgs* __restrict__ as) {
+  sel_finish_body(as[blockIdx.y]);
 }
 
 // ------------------------------------------------------------------ masked echo
@@ -739,7 +784,33 @@ cudaError_t launch_niht_mu_mode(const SelArgs& a, int first, cudaStream_t s) {
 }
 cudaError_t launch_niht_mu(const SelArgs& a, cudaStream_t s) { return launch_niht_mu_mode(a, 0, s); }
 cudaError_t sel_set_attributes() {
-  return cudaFuncSetAttribute(k_sel_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_sel_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sel_fused_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  return e;
+}
+
+// One launch of selection kernel k for every patch of a batch: as[p] are patch p's
+// arguments (device memory); single-CTA kernels get one CTA per patch, grid-stride
+// kernels a share of the grid per patch (blockIdx.y = patch).  arg: level or raw.
+cudaError_t launch_sel_batched(SelKernel k, const SelArgs* as, int np, int arg, cudaStream_t s) {
+  if (np <= 0) return cudaSuccess;
+  const dim3 one(1, np);
+  const int gx0 = (grid_ctas() + np - 1) / np;
+  const dim3 grid(gx0 < 2 ? 2 : gx0, np);
+  switch (k) {
+    case SelKernel::kCheck: k_sel_check_b<<<one, kSelThreads, 0, s>>>(as); break;
+    case SelKernel::kCheck2: k_sel_check2_b<<<one, kSelThreads, 0, s>>>(as); break;
+    case SelKernel::kRound: k_sel_round_b<<<grid, kGridThreads, 0, s>>>(as, arg); break;
+    case SelKernel::kPick: k_sel_pick_b<<<one, kSelThreads, 0, s>>>(as, arg); break;
+    case SelKernel::kCount: k_thr_count_b<<<grid, kGridThreads, 0, s>>>(as); break;
+    case SelKernel::kScan: k_thr_scan_b<<<one, kSelThreads, 0, s>>>(as); break;
+    case SelKernel::kScatter: k_thr_scatter_b<<<grid, kGridThreads, 0, s>>>(as, arg); break;
+    case SelKernel::kFused: k_sel_fused_b<<<one, kSelThreads, kFusedSmem, s>>>(as); break;
+    case SelKernel::kFinish: k_sel_finish_b<<<one, kSelThreads, 0, s>>>(as); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 cudaError_t launch_sel_fused(const SelArgs& a, cudaStream_t s) {
   k_sel_fused<<<1, kSelThreads, kFusedSmem, s>>>(a);

@@ -103,3 +103,20 @@ def test_rda_plan_checks_on_host():
         assert h.value is None
         msg = csar.lib.csar_last_error().decode()
         assert ("slope" in msg) or ("Doppler" in msg) or ("phase" in msg), msg
+
+
+def test_batch_member_flag_checked_on_host():
+    """CSAR_PLAN_BATCH_MEMBER: sizes the one-launch-per-pass batch kernels do not serve
+    are refused (CSAR_E_UNSUPPORTED), and so is the flag with another column flag
+    (CSAR_E_INVALID), before any CUDA call."""
+    import synth
+    from paper_1302_3120_gb300 import csar
+    h = ctypes.c_void_p()
+    for na, nr in [(256, 512), (512, 8192), (8192, 1024)]:
+        p = csar.params_of(synth.airborne(na, nr))
+        assert csar.lib.csar_plan_create(ctypes.byref(p), csar.PLAN_BATCH_MEMBER, ctypes.byref(h)) == 2
+        assert h.value is None and "batch member" in csar.lib.csar_last_error().decode()
+    p = csar.params_of(synth.airborne(1024, 1024))
+    for other in (csar.PLAN_COL_HALF_TILE, csar.plan_col_cluster(2), csar.PLAN_RDA, csar.PLAN_COL_PERSIST):
+        assert csar.lib.csar_plan_create(ctypes.byref(p), csar.PLAN_BATCH_MEMBER | other, ctypes.byref(h)) == 1
+        assert h.value is None

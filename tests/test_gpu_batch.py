@@ -1,6 +1,8 @@
 """Batched ITA over patches of uneven size (spec batching row): one graph launch
-per iteration with one branch per patch gives the same images as the per-patch loop,
-matches the oracle, and the autotuner picks a working column configuration."""
+per iteration, holding one launch per pass over a work table of every patch when all
+sizes are served by the batched kernels (512 to 4096 per axis), else one branch per
+patch, gives the same images as the per-patch loop, matches the oracle, and the
+autotuner picks a working column configuration."""
 import numpy as np
 import pytest
 
@@ -100,11 +102,16 @@ def test_batched_real_patch_mix():
     batch = csar.csar_batch_create(geoms)
     Xb = csar.csar_solve_batched(batch, Ys, Ms, Ks, iters)
     csar.csar_batch_check(batch)
+    # every size is served by the batched kernels: one launch per pass, and each patch's
+    # image equals that of a plan configured as a batch member
     for i, g in enumerate(geoms):
-        plan = csar.csar_plan_create(g)
+        plan = csar.csar_plan_create(g, flags=csar.PLAN_BATCH_MEMBER)
         Xl = csar.csar_solve(plan, Ys[i], Ms[i], Ks[i], iters)
         assert torch.equal(Xb[i], Xl), i
         plan.close()
+    # a second solve on the same batch replays the captured graphs
+    Xb2 = csar.csar_solve_batched(batch, Ys, Ms, Ks, iters)
+    assert all(torch.equal(a, b) for a, b in zip(Xb, Xb2))
     for i in checked.values():
         g = geoms[i]
         x_ref, _ = ita.ita(g, host_y[i], masks[i], Ks[i], iters)
