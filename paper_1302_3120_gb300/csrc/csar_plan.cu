@@ -549,6 +549,8 @@ SelArgs sel_args(csar_plan plan, int cur, const csar_opts& o) {
   s.n = plan->n;
   s.nr = plan->nr;
   s.col_tile = plan->col_tile;
+  s.tile_shift = 0;
+  while ((1 << s.tile_shift) < plan->col_tile) ++s.tile_shift;
   s.n_tiles = plan->n_tiles;
   s.thresh = o.thresh;
   s.mu_mode = o.mu_mode;

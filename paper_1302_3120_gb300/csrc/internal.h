@@ -299,6 +299,7 @@ struct SelArgs {
   int64_t n;
   int nr;
   int col_tile;               // columns per column-pass tile
+  int tile_shift;             // log2(col_tile) (n_rg and col_tile are powers of two)
   int n_tiles;
   int thresh;                 // 0 soft, 1 half, 2 hard
   int mu_mode;                // 0 fixed, 1 NIHT

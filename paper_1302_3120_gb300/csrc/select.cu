@@ -32,6 +32,11 @@ constexpr int kGridThreads = 512;   // grid-stride kernels
 
 __device__ __forceinline__ uint32_t key_of(float2 b) { return __float_as_uint(cabs2(b)) & 0x7fffffffu; }
 
+// Column tile of flat index idx = row * n_rg + col (shifts: both sizes are powers of two).
+__device__ __forceinline__ uint32_t tile_of(const SelArgs& a, uint32_t idx) {
+  return (idx & (uint32_t)(a.nr - 1)) >> a.tile_shift;
+}
+
 // b of union element e: on-support entries first (X + mu dX), then candidates (mu dX).
 __device__ __forceinline__ float2 union_b(const SelArgs& a, uint32_t e, uint32_t nx, float mu,
                                           uint32_t* idx) {
@@ -355,7 +360,7 @@ __device__ __forceinline__ void thr_count_body(const SelArgs& a) {
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nu; e += gridDim.x * blockDim.x) {
     uint32_t idx;
     const uint32_t key = key_of(union_b(a, e, nx, mu, &idx));
-    if (kept(key, s2)) atomicAdd(&a.tile_cnt[(idx % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+    if (kept(key, s2)) atomicAdd(&a.tile_cnt[tile_of(a, idx)], 1u);
     else if (key == s2 && s2 >= kMinKey) atomicMin(&c->jstar, idx);   // the (K+1)-th element
   }
 }
@@ -410,7 +415,7 @@ __device__ __forceinline__ void thr_scatter_body(const SelArgs& a, int raw) {
     const float2 b = union_b(a, e, nx, mu, &idx);
     if (idx == jstar) c->b_jstar = b;
     if (!kept(key_of(b), s2)) continue;
-    const uint32_t tile = (idx % (uint32_t)a.nr) / (uint32_t)a.col_tile;
+    const uint32_t tile = tile_of(a, idx);
     const uint32_t pos = atomicAdd(&a.tile_cur[tile], 1u);
     if (!CSAR_CHECK(pos, a.n, c) || !CSAR_CHECK(idx, a.n, c)) continue;
     a.xo_idx[pos] = idx;
@@ -445,6 +450,9 @@ __device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
   // one CTA has few threads for the latency of these loads: each thread keeps kU
   // elements' loads in flight at a time
   constexpr int kU = 8;
+  // keys into shared memory, with the first radix round's histogram (12 high key bits)
+  for (int i = tid; i < (int)kHistBins; i += kSelThreads) h[i] = 0u;
+  __syncthreads();
   for (uint32_t e0 = tid; e0 < nu; e0 += kU * kSelThreads) {
     float2 bv[kU];
 #pragma unroll
@@ -456,7 +464,11 @@ __device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const uint32_t e = e0 + u * kSelThreads;
-      if (e < nu) key[e] = key_of(bv[u]);
+      if (e < nu) {
+        const uint32_t k = key_of(bv[u]);
+        key[e] = k;
+        if (k >= kMinKey) atomicAdd(&h[k >> 20], 1u);
+      }
     }
   }
   // three radix rounds (12 + 12 + 8 key bits) on the keys in shared memory
@@ -465,14 +477,15 @@ __device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
   bool all = false;
   for (int level = 0; level < 3; ++level) {
     const int nb = level == 2 ? 256 : (int)kHistBins;
-    for (int i = tid; i < nb; i += kSelThreads) h[i] = 0u;
-    __syncthreads();
-    for (uint32_t e = tid; e < nu; e += kSelThreads) {
-      const uint32_t k = key[e];
-      if (k < kMinKey) continue;
-      if (level == 0) atomicAdd(&h[k >> 20], 1u);
-      else if (level == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 4095u], 1u); }
-      else if ((k >> 8) == prefix) atomicAdd(&h[k & 255u], 1u);
+    if (level > 0) {
+      for (int i = tid; i < nb; i += kSelThreads) h[i] = 0u;
+      __syncthreads();
+      for (uint32_t e = tid; e < nu; e += kSelThreads) {
+        const uint32_t k = key[e];
+        if (k < kMinKey) continue;
+        if (level == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 4095u], 1u); }
+        else if ((k >> 8) == prefix) atomicAdd(&h[k & 255u], 1u);
+      }
     }
     __syncthreads();
     uint64_t above = 0;
@@ -505,7 +518,7 @@ __device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
     for (int u = 0; u < kU; ++u) {
       if (ix[u] == 0xffffffffu) continue;
       const uint32_t e = e0 + u * kSelThreads;
-      if (kept(key[e], s2)) atomicAdd(&tcnt[(ix[u] % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+      if (kept(key[e], s2)) atomicAdd(&tcnt[tile_of(a, ix[u])], 1u);
       else atomicMin(&s_jstar, ix[u]);
     }
   }
@@ -549,7 +562,7 @@ __device__ __forceinline__ void sel_fused_body(const SelArgs& a) {
       const uint32_t e = e0 + u * kSelThreads;
       if (ix[u] == jstar) c->b_jstar = bv[u];
       if (!kept(key[e], s2)) continue;
-      const uint32_t pos = atomicAdd(&tcnt[(ix[u] % (uint32_t)a.nr) / (uint32_t)a.col_tile], 1u);
+      const uint32_t pos = atomicAdd(&tcnt[tile_of(a, ix[u])], 1u);
       if (!CSAR_CHECK(pos, a.n, c) || !CSAR_CHECK(ix[u], a.n, c)) continue;
       a.xo_idx[pos] = ix[u];
       a.xo_val[pos] = shrink(bv[u], sigma, a.thresh);
