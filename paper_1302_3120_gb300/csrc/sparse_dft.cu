@@ -3,13 +3,16 @@
 // The first column pass of G(X) transforms X^(i), which has at most K nonzeros
 // (K = 20000 on 8192 x 8192: ~2.4 per column).  For a group of 16 columns holding
 // few entries, X[k, col] = sum_e x_e W_N^(k row_e) is cheaper than an N-point FFT:
-// the group's entries are bucketed by column in shared memory, one warp per column
-// accumulates its own entries for 8 output rows per lane (the twiddle advances by
-// W_N^(32 row_e) per row step from an exact table start), and a 256 x 16 block is
+// the group's entries are bucketed by column in shared memory and a warp accumulates a
+// column's entries for 8 output rows per lane (the twiddle advances by W_N^(32 row_e) per
+// row step from an exact table start).  Entry counts per column vary (Poisson, mean ~2.4),
+// so two chunks of rows are in flight, one per group of 8 warps, and a warp takes a
+// heaviest-with-lightest pair of columns of its chunk.  Each 256 x 16 block is
 // staged in shared memory and written to global memory by one tensor copy
 // (cp.async.bulk.tensor, 128-byte rows, 128-byte swizzle so that the column-wise
-// staging writes spread over the banks), double-buffered so that the copy of one chunk
-// overlaps the sums of the next: the pass issues no per-element store instructions.
+// staging writes spread over the banks), one staging block per chunk in flight; the
+// copies of a chunk pair overlap the lightest columns' sums of the next pair, and the
+// pass issues no per-element store instructions.
 // Groups with more entries are left to the FFT path (k_col, COL_SPARSE_FWD).
 #include <cuda.h>
 
@@ -26,7 +29,7 @@ constexpr int kSdBlkBytes = kSdRows * kDirectCols * (int)sizeof(float2);   // 32
 // twiddles and the entry lists
 constexpr size_t kSdSmem = 1024 + 2 * kSdBlkBytes + (kTwLo + kTwHi) * sizeof(float2) +
                            kDirectMaxEntries * (2 * sizeof(uint32_t) + sizeof(float2)) +
-                           (kDirectCols + 1) * sizeof(int);
+                           (2 * kDirectCols + 1) * sizeof(int);
 
 // Byte offset of element (r, c) of a staging block: rows of 128 bytes whose 16-byte
 // chunks are permuted by XOR with r mod 8 (the tensor map's 128-byte swizzle).
@@ -45,6 +48,7 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(const __grid_constant
   uint32_t* e_row = e_key + kDirectMaxEntries;
   float2* e_val = reinterpret_cast<float2*>(e_row + kDirectMaxEntries);
   int* col_beg = reinterpret_cast<int*>(e_val + kDirectMaxEntries);
+  int* col_order = col_beg + kDirectCols + 1;   // columns by entry count, heaviest first
   if (a.gate && *a.gate != a.gate_val) return;
   const int grp = blockIdx.x;
   const int bpg = kDirectCols / col_tile > 0 ? kDirectCols / col_tile : 1;
@@ -89,16 +93,31 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(const __grid_constant
     col_beg[tid] = cnt;
   }
   __syncthreads();
+  if (tid < kDirectCols) {
+    // position of column tid in the order by entry count (descending; ties by column)
+    const int mine = col_beg[tid + 1] - col_beg[tid];
+    int pos = 0;
+    for (int cc = 0; cc < kDirectCols; ++cc) {
+      const int n = col_beg[cc + 1] - col_beg[cc];
+      pos += (n > mine) || (n == mine && cc < tid);
+    }
+    col_order[pos] = tid;
+  }
+  __syncthreads();
+  // Two chunks in flight, one per group of 8 warps; warp w sums the (w % 8)-th heaviest
+  // and the (w % 8)-th lightest column of its group's chunk (8 rows per lane each), so a
+  // chunk pair waits for the heaviest column pair instead of one chunk for the heaviest
+  // column.
   const int w = tid >> 5, lane = tid & 31;
-  const int i0 = col_beg[w], i1 = col_beg[w + 1];
+  const int g = w >> 3;
+  const int c_light = col_order[kDirectCols - 1 - (w & 7)], c_heavy = col_order[w & 7];
   constexpr int kScale = kTwN / N;            // W_N^m = W_8192^(m * kScale)
   const bool in_range = CSAR_CHECK((size_t)col0 + kDirectCols - 1, (size_t)a.nr, a.ctl);
-  for (int ch = 0; ch < chunks_per_cta; ++ch) {
-    const int k0 = (blockIdx.y * chunks_per_cta + ch) * kSdRows;
-    float2 acc[8];
+  auto column_sum = [&](int cl, int k0, float2 (&acc)[8]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int i = i0; i < i1; ++i) {           // uniform per warp
+    const int i1 = col_beg[cl + 1];
+    for (int i = col_beg[cl]; i < i1; ++i) {   // uniform per warp
       const uint32_t row = e_row[i];
       const float2 x = e_val[i];
       float2 e = cmul(x, twiddle_tab<false>(tw, (int)(((uint32_t)(k0 + lane) * row) % N) * kScale));
@@ -109,21 +128,36 @@ __global__ void __launch_bounds__(kSdThreads) k_sparse_dft(const __grid_constant
         e = cmul(e, st);
       }
     }
-    // staging block ch % 2 is free once the copy issued two chunks ago has read it
-    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+  };
+  for (int ch0 = 0; ch0 < chunks_per_cta; ch0 += 2) {
+    const int ch = ch0 + g;
+    const bool act = ch < chunks_per_cta;
+    const int k0 = (blockIdx.y * chunks_per_cta + ch) * kSdRows;
+    unsigned char* const bk = blk + g * kSdBlkBytes;
+    float2 acc[8];
+    if (act) column_sum(c_light, k0, acc);
+    // both staging blocks are free once the copies of the previous chunk pair have read them
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();
-    unsigned char* const bk = blk + (ch & 1) * kSdBlkBytes;
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) *reinterpret_cast<float2*>(bk + blk_off(lane + 32 * j, w)) = acc[j];
-    // the staging writes become visible to the tensor copy (async proxy)
+      for (int j = 0; j < 8; ++j) *reinterpret_cast<float2*>(bk + blk_off(lane + 32 * j, c_light)) = acc[j];
+      column_sum(c_heavy, k0, acc);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) *reinterpret_cast<float2*>(bk + blk_off(lane + 32 * j, c_heavy)) = acc[j];
+    }
+    // the staging writes become visible to the tensor copies (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0 && in_range && CSAR_CHECK((size_t)k0 + kSdRows - 1, (size_t)N, a.ctl)) {
-      asm volatile(
-          "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n\t"
-          "cp.async.bulk.commit_group;" ::"l"(&omap),
-          "r"(col0), "r"(k0), "r"(sbase + (uint32_t)((ch & 1) * kSdBlkBytes))
-          : "memory");
+    if (tid == 0 && in_range) {
+      for (int gg = 0; gg < 2 && ch0 + gg < chunks_per_cta; ++gg) {
+        const int kk = (blockIdx.y * chunks_per_cta + ch0 + gg) * kSdRows;
+        if (!CSAR_CHECK((size_t)kk + kSdRows - 1, (size_t)N, a.ctl)) continue;
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                     ::"l"(&omap), "r"(col0), "r"(kk), "r"(sbase + (uint32_t)(gg * kSdBlkBytes))
+                     : "memory");
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
   }
   // the copies complete (their writes performed) before the CTA's shared memory is released
